@@ -1,0 +1,132 @@
+"""Oracle for the four-phonon scattering-rate path: TEST INFRASTRUCTURE ONLY.
+
+Only `tests/`, `__graft_entry__.smoke()` and the benchmark's CPU-baseline leg
+may import this package.  It shares no code with the CUDA path (no kernels,
+headers, helpers, tables or constants); both sides only read the seeded inputs
+of `paper_2104_04895_gb300.synth`.
+
+* `fp_oracle.c`  plain FP64 C (OpenMP) rates and vertices (Eqs. tao0, 4phgamma, V4; Sec. 2.4)
+* `modes.py`     harmonic frequencies, eigenvectors, velocities (numpy / LAPACK)
+* `brute.py`     supercell brute-force vertex for tiny grids
+* `mlp.py`       FP64 forward/backward of the surrogate network (for gradient checks)
+
+Every function is pinned by the `-m "not gpu"` tests in `tests/test_oracle_*.py`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+
+def build(force: bool = False) -> str:
+    """Compile fp_oracle.c into oracle/_build/liboracle.so (gcc, OpenMP, no FP contraction)."""
+    out_dir = os.path.join(_HERE, "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    so = os.path.join(out_dir, "liboracle.so")
+    src = os.path.join(_HERE, "fp_oracle.c")
+    if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+        tmp = so + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                               "-fno-fast-math", "-D_GNU_SOURCE", "-o", tmp, src, "-lm"])
+        os.replace(tmp, so)
+    return so
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        L = ctypes.CDLL(build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        L.oracle_rates4.restype = ctypes.c_int
+        L.oracle_rates4.argtypes = [ip, dp, ctypes.c_int, dp, ctypes.c_int, ip, dp, dp, dp, dp,
+                                    ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_int, ctypes.c_int, ip, ctypes.c_int, ctypes.c_int, dp, dp]
+        L.oracle_v4.restype = ctypes.c_int
+        L.oracle_v4.argtypes = [ip, dp, ctypes.c_int, dp, ctypes.c_int, ip, dp, dp, ctypes.c_int,
+                                ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, ip]
+        L.oracle_bose.restype = ctypes.c_double
+        L.oracle_bose.argtypes = [ctypes.c_double, ctypes.c_double]
+        L.oracle_prefactor.restype = ctypes.c_double
+        L.oracle_prefactor.argtypes = [ctypes.c_int]
+        _LIB = L
+    return _LIB
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _i(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def evec_to_array(ev):
+    """complex (N, nb, nb) -> float (N, nb, nb, 2)"""
+    return np.ascontiguousarray(np.stack([ev.real, ev.imag], axis=-1))
+
+
+def rates4(cryst, omega, evec, vel, temps=None, scalebroad=None, window=2.0, sigma_min=1e-10, dq_mode=0,
+           sel=None, unit_vertex=False, nthreads=0):
+    """Rates (nT, nsel) in ps^-1 and accepted counts (3,) for modes sel (default: all)."""
+    temps = cryst.temps if temps is None else temps
+    sb = cryst.scalebroad if scalebroad is None else scalebroad
+    nb = cryst.nb
+    N = cryst.nq
+    if sel is None:
+        sel = np.arange(N * nb)
+    sel_a, sel_p = _i(np.asarray(sel))
+    grid, grid_p = _i(np.asarray(cryst.grid))
+    lat, lat_p = _d(cryst.lattice)
+    m, m_p = _d(cryst.mass)
+    qi, qi_p = _i(cryst.fc4_idx)
+    qf, qf_p = _d(cryst.fc4_val)
+    om, om_p = _d(omega)
+    ev, ev_p = _d(evec_to_array(evec) if np.iscomplexobj(evec) else evec)
+    ve, ve_p = _d(vel)
+    T, T_p = _d(np.asarray(temps, float))
+    out = np.zeros((len(temps), len(sel_a)))
+    acc = np.zeros(3)
+    _, out_p = _d(out)
+    out_p = out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    acc_p = acc.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    rc = lib().oracle_rates4(grid_p, lat_p, cryst.natoms, m_p, len(qi), qi_p, qf_p, om_p, ev_p, ve_p,
+                             len(T), T_p, float(sb), float(window), float(sigma_min), int(dq_mode),
+                             len(sel_a), sel_p, int(bool(unit_vertex)), int(nthreads), out_p, acc_p)
+    if rc != 0:
+        raise ValueError("oracle_rates4 rejected its arguments")
+    return out, acc
+
+
+def v4(cryst, evec, q, q1, q2, process):
+    """Branch tensor V[j, j1, j2, j3] (complex) of process 0:++, 1:+-, 2:-- and q'''."""
+    nb = cryst.nb
+    grid, grid_p = _i(np.asarray(cryst.grid))
+    lat, lat_p = _d(cryst.lattice)
+    m, m_p = _d(cryst.mass)
+    qi, qi_p = _i(cryst.fc4_idx)
+    qf, qf_p = _d(cryst.fc4_val)
+    ev, ev_p = _d(evec_to_array(evec) if np.iscomplexobj(evec) else evec)
+    out = np.zeros((nb, nb, nb, nb, 2))
+    q3 = ctypes.c_int(0)
+    rc = lib().oracle_v4(grid_p, lat_p, cryst.natoms, m_p, len(qi), qi_p, qf_p, ev_p, int(q), int(q1), int(q2),
+                         int(process), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(q3))
+    if rc != 0:
+        raise ValueError("oracle_v4 rejected its arguments")
+    return out[..., 0] + 1j * out[..., 1], q3.value
+
+
+def bose(w, T):
+    return lib().oracle_bose(float(w), float(T))
+
+
+def prefactor(nq):
+    return lib().oracle_prefactor(int(nq))

@@ -1,0 +1,176 @@
+"""Pins of the oracle's rates (Eqs. tao0 and 4phgamma, the Gaussian delta of Sec. 2.4).
+
+* a single-q (1x1x1) crystal with injected integer frequencies and zero velocities, where
+  only exactly energy-conserving terms enter with delta := 1 (the small-sigma rule of
+  Sec. 2.4): the rate is recomputed term by term in SI units from the brute-force
+  supercell vertex, which pins the prefactor, the unit conversion, the multiplicities
+  1/2, 1/2, 1/6 and the three Bose forms;
+* the on-shell detailed-balance identities of the Bose combinations;
+* the classical limit rate(2T)/rate(T) -> 4;
+* exact quadratic scaling in Phi4 and zero rates at Phi4 = 0;
+* equal rates at symmetry-equivalent q for point-group-symmetric force constants;
+* accepted-term counts from an independent vectorised enumeration of the window rule.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import oracle.brute as brute
+import oracle.modes as om
+from paper_2104_04895_gb300 import synth
+from conftest import oracle_modes
+
+HBAR_SI = 1.054571817e-34     # J s
+KB_SI = 1.380649e-23          # J/K
+EV = 1.602176634e-19
+AMU_SI = 1.66053906660e-27
+ANG = 1e-10
+
+
+def bose_si(w_rad_ps, T):
+    return 1.0 / np.expm1(HBAR_SI * w_rad_ps * 1e12 / (KB_SI * T))
+
+
+def test_single_q_closed_form_in_si_units(rng):
+    cr = synth.diamond_si((1, 1, 1))
+    nb = cr.nb
+    omega = np.array([[3.0, 1.0, 1.0, 1.0, 7.0, 11.0]])
+    # random unitary eigenvectors (complex, so that the conjugated legs matter)
+    A = rng.normal(size=(nb, nb)) + 1j * rng.normal(size=(nb, nb))
+    Q, _ = np.linalg.qr(A)
+    evec = Q.T[None, :, :].copy()
+    vel = np.zeros((1, nb, 3))
+    T = 300.0
+    rates, acc = oracle.rates4(cr, omega, evec, vel, temps=[T], scalebroad=1.0)
+    P = brute.supercell_phi4(cr)
+    mult = {0: 0.5, 1: 0.5, 2: 1.0 / 6.0}
+    signs = {0: (1, 1), 1: (1, -1), 2: (-1, -1)}
+    # brute-force vertex in eV/(A^4 amu^2) -> SI J/(m^4 kg^2)
+    vconv = EV / ANG**4 / AMU_SI**2
+    n = bose_si(omega[0], T)
+    count = np.zeros(3)
+    for lam in range(nb):
+        expect = 0.0
+        for pr in range(3):
+            s1, s2 = signs[pr]
+            V = brute.vertex(cr, P, evec, 0, 0, 0, 0, conj1=s1 < 0, conj2=s2 < 0)
+            for j1 in range(nb):
+                for j2 in range(nb):
+                    for j3 in range(nb):
+                        dw = omega[0, lam] + s1 * omega[0, j1] + s2 * omega[0, j2] - omega[0, j3]
+                        if dw != 0.0:
+                            continue
+                        count[pr] += 1
+                        if pr == 0:
+                            B = (1 + n[j1]) * (1 + n[j2]) * n[j3]
+                        elif pr == 1:
+                            B = (1 + n[j1]) * n[j2] * n[j3]
+                        else:
+                            B = n[j1] * n[j2] * n[j3]
+                        wsi = omega[0, [lam, j1, j2, j3]] * 1e12
+                        # Gamma_p = hbar^2 pi / (8N) B/n |V|^2 delta / prod(w); delta = 1 ps = 1e-12 s; N = 1
+                        gam = HBAR_SI**2 * np.pi / 8.0 * B / n[lam] * abs(V[lam, j1, j2, j3] * vconv) ** 2 \
+                            * 1e-12 / np.prod(wsi)
+                        expect += mult[pr] * gam
+        expect_ps = expect * 1e-12
+        assert rates[0, lam] == pytest.approx(expect_ps, rel=1e-9, abs=1e-300), lam
+    assert np.array_equal(acc, count)
+    assert acc.min() > 0  # every process is exercised
+
+
+def test_detailed_balance_on_shell():
+    for T in (50.0, 300.0, 1000.0):
+        for (w, w1, w2) in [(1.0, 2.0, 3.5), (10.0, 0.3, 7.0), (25.0, 20.0, 1.0)]:
+            n = lambda x: oracle.bose(x, T)
+            # ++ : w''' = w + w' + w''
+            w3 = w + w1 + w2
+            lhs = (1 + n(w1)) * (1 + n(w2)) * n(w3) / n(w)
+            rhs = n(w1) * n(w2) * (1 + n(w3)) / (1 + n(w))
+            assert lhs == pytest.approx(rhs, rel=1e-12)
+            # +- : w + w' = w'' + w'''
+            w3 = w + w1 - w2 if w + w1 - w2 > 0 else None
+            if w3:
+                lhs = (1 + n(w1)) * n(w2) * n(w3) / n(w)
+                rhs = n(w1) * (1 + n(w2)) * (1 + n(w3)) / (1 + n(w))
+                assert lhs == pytest.approx(rhs, rel=1e-12)
+            # -- : w = w' + w'' + w'''
+            W = w1 + w2 + 4.0
+            lhs = n(w1) * n(w2) * n(4.0) / n(W)
+            rhs = (1 + n(w1)) * (1 + n(w2)) * (1 + n(4.0)) / (1 + n(W))
+            assert lhs == pytest.approx(rhs, rel=1e-12)
+    # Bose values against the SI definition
+    for w in (0.1, 5.0, 50.0):
+        assert oracle.bose(w, 300.0) == pytest.approx(bose_si(w, 300.0), rel=1e-9)
+
+
+def test_classical_limit_quadratic_in_T():
+    cr = synth.simple_cubic((3, 3, 3))
+    w, e, v = oracle_modes(cr)
+    sel = [3 * 5 + 1, 3 * 13 + 2]
+    r, _ = oracle.rates4(cr, w, e, v, temps=[1e6, 2e6], sel=sel)
+    ratio = r[1] / r[0]
+    np.testing.assert_allclose(ratio, 4.0, rtol=2e-3)
+
+
+def test_quadratic_scaling_and_zero():
+    cr = synth.simple_cubic((3, 3, 2))
+    w, e, v = oracle_modes(cr)
+    r1, a1 = oracle.rates4(cr, w, e, v)
+    r2, a2 = oracle.rates4(cr.scaled_fc4(2.0), w, e, v)
+    assert np.array_equal(r2, 4.0 * r1)
+    assert np.array_equal(a1, a2)
+    r0, a0 = oracle.rates4(cr.scaled_fc4(0.0), w, e, v)
+    assert np.all(r0 == 0.0) and np.array_equal(a0, a1)
+    assert r1.max() > 0
+
+
+def _avg_degenerate(rates_row, omega_row):
+    out = rates_row.copy()
+    for (b, e_) in om.degenerate_sets(omega_row):
+        out[b:e_] = rates_row[b:e_].mean()
+    return out
+
+
+def test_symmetry_equivalent_q_have_equal_rates():
+    cr = synth.simple_cubic((4, 4, 4), symmetric=True)
+    w, e, v = oracle_modes(cr)
+    nb = cr.nb
+    # grid points related by the cubic group: (1,0,0), (0,1,0), (0,0,3) and (1,2,0), (2,0,3)
+    groups = [[(1, 0, 0), (0, 1, 0), (0, 0, 3), (3, 0, 0)], [(1, 2, 0), (2, 0, 3), (0, 3, 2)]]
+    for grp in groups:
+        qs = [(g[0] * 4 + g[1]) * 4 + g[2] for g in grp]
+        sel = [q * nb + j for q in qs for j in range(nb)]
+        r, _ = oracle.rates4(cr, w, e, v, sel=sel)
+        rows = [_avg_degenerate(r[0, k * nb:(k + 1) * nb], w[qs[k]]) for k in range(len(qs))]
+        for k in range(1, len(qs)):
+            np.testing.assert_allclose(rows[k], rows[0], rtol=1e-9)
+
+
+def test_accepted_counts_by_enumeration():
+    cr = synth.simple_cubic((3, 3, 3))
+    w, e, v = oracle_modes(cr)
+    nb, N = cr.nb, cr.nq
+    G = om.grid_points(cr.grid)
+    ng = np.array(cr.grid)
+    B = om.reciprocal(cr.lattice)
+    dq = (abs(np.linalg.det(B)) / N) ** (1.0 / 3.0)
+    sel = [nb * 4 + 1, nb * 10 + 2, nb * 22]
+    _, acc = oracle.rates4(cr, w, e, v, sel=sel, window=2.0)
+    count = np.zeros(3)
+    for m in sel:
+        q, j = divmod(m, nb)
+        for pr, (s1, s2) in enumerate([(1, 1), (1, -1), (-1, -1)]):
+            g3 = (G[q][None, None, :] + s1 * G[:, None, :] + s2 * G[None, :, :]) % ng
+            q3 = (g3[..., 0] * ng[1] + g3[..., 1]) * ng[2] + g3[..., 2]          # (q1, q2)
+            W1 = w[:, None, :, None, None]                                     # q1, -, j1
+            W2 = w[None, :, None, :, None]                                     # -, q2, -, j2
+            W3 = w[q3][:, :, None, None, :]                                    # q1, q2, -, -, j3
+            t = (w[q, j] + s1 * W1) + s2 * W2
+            dw = t - W3
+            V2 = v[None, :, None, :, None, :]
+            V3 = v[q3][:, :, None, None, :, :]
+            d = V2 - V3
+            sig = (1.0 * np.sqrt((d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1]) + d[..., 2] * d[..., 2])) * dq
+            ok = (np.abs(dw) <= 2.0 * np.where(sig < 1e-10, 1e-10, sig)) & (W1 != 0) & (W2 != 0) & (W3 != 0)
+            count[pr] += ok.sum()
+    assert np.array_equal(acc, count)
