@@ -1,0 +1,295 @@
+#!/usr/bin/env python
+"""Benchmark: four-phonon process-terms/s for one full-grid RTA rate set on GB300.
+
+Workload (default): diamond Si-like crystal, 2 atoms (nb = 6), 8x8x8 q-grid, T = 300 K,
+scalebroad 1.0 -- the configuration the headline metric is quoted on.  A step is one
+full-grid rate set: Bose weights, the fused persistent rate kernel (vertex assembly,
+contraction, window, Gaussian, accumulation) and the fixed-order reduction.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `value` is candidate process terms per second with the
+modes resident in HBM; `e2e` is the same metric through the public C-ABI calls with host
+buffers (fp_init + fp_modes + fp_rates4 + fp_free per step); `cpu_baseline` is the FP64
+oracle timed on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2104_04895_gb300 import synth  # noqa: E402
+
+FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (recipe nominal; 152 SMs x 2070 MHz x 2 DFMA/clk/SM x 2 = 1.26)
+FP32_PEAK_TFLOPS = 80.5   # 152 SMs x 2070 MHz x 128 FFMA/clk/SM x 2
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    p.add_argument("--workload", type=int, default=2)
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--cpu-sample-seconds", type=float, default=15.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def shard(N, ws, rank):
+    return (N * rank) // ws, (N * (rank + 1)) // ws
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(cr, seconds, w=None, e=None, v=None):
+    """FP64 oracle on sampled modes with full partner sums, until about `seconds` of CPU work."""
+    import oracle
+    import oracle.modes as om
+    if w is None:
+        w, e, v = om.modes(cr)
+    rng = np.random.Generator(np.random.PCG64(2104))
+    order = rng.permutation(np.arange(cr.nb, cr.nq * cr.nb))
+    cores = os.cpu_count() or 1
+    sel, ref, t_total = [], [], 0.0
+    for m in order:
+        t0 = time.perf_counter()
+        r, _ = oracle.rates4(cr, w, e, v, sel=[int(m)], nthreads=cores)
+        t_total += time.perf_counter() - t0
+        sel.append(int(m))
+        ref.append(r[:, 0])
+        if t_total >= seconds:
+            break
+    cands = 3.0 * len(sel) * cr.nq ** 2 * cr.nb ** 3
+    return {"value": cands / t_total, "unit": "process-terms/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(sel)} modes of {cr.name} {cr.grid[0]}x{cr.grid[1]}x{cr.grid[2]} with full (q',q'') "
+                      f"partner sums, {t_total:.1f} s", "seconds": t_total}, sel, np.array(ref).T
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    cr = synth.workload(args.workload)
+    import oracle
+    import oracle.modes as om
+    w, e, v = om.modes(cr)
+    cores = os.cpu_count() or 1
+    rng = np.random.Generator(np.random.PCG64(7))
+    order = rng.permutation(np.arange(cr.nb, cr.nq * cr.nb))
+    per_step = 1
+    times = []
+    for s in range(args.warmup + args.steps):
+        sel = [int(m) for m in order[s * per_step:(s + 1) * per_step]]
+        t0 = time.perf_counter()
+        oracle.rates4(cr, w, e, v, sel=sel, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    cands = 3.0 * per_step * cr.nq ** 2 * cr.nb ** 3
+    val = cands * len(times) / sum(times)
+    line = {"impl": "reference", "metric": "four-phonon process-terms/s", "value": val, "unit": "process-terms/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": synth.WORKLOAD_NAMES[args.workload], "sample_modes_per_step": per_step},
+            "cpu_baseline": {"value": val, "unit": "process-terms/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} mode(s) per step with full partner sums"},
+            "e2e": {"value": val, "unit": "process-terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+    from paper_2104_04895_gb300 import binding
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = binding.FP_PREC_FP64 if args.precision == "fp64" else binding.FP_PREC_MIXED
+    cr = synth.workload(args.workload)
+    N, nb, nT = cr.nq, cr.nb, len(cr.temps)
+    q0, q1 = shard(N, ws, rank)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    ctx = binding.Context.from_crystal(cr, device=local)
+    stream = torch.cuda.current_stream(dev)
+    ctx.set_stream(stream.cuda_stream)
+    w, e, v = ctx.modes()
+    out = torch.zeros(nT * N * nb, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > 129 MB L2
+
+    def step():
+        return ctx.rates4_device(cr.temps, out.data_ptr(), cr.scalebroad, precision=prec, q_begin=q0, q_end=q1)
+
+    for _ in range(args.warmup):
+        st = step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kernel_ms = []
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            st = step()
+            ev[i][1].record(stream)
+            kernel_ms.append(st["ms"])
+        torch.cuda.synchronize()
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if ws > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    cands_step = 3.0 * N * N * N * nb ** 4          # all ranks together: one full-grid rate set per step
+    value = cands_step * args.steps / (total_ms * 1e-3)
+    flops_launch = st["flops"]
+    kms = float(np.mean(kernel_ms))
+    achieved_tflops = flops_launch / (kms * 1e-3) / 1e12
+    peak = FP64_PEAK_TFLOPS if prec == binding.FP_PREC_FP64 else FP32_PEAK_TFLOPS
+
+    # end to end through the public API with host buffers
+    e2e_times = []
+    h2d = d2h = 0
+    for i in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        with binding.Context.from_crystal(cr, device=local) as c2:
+            c2.modes(copy=False)
+            r, _ = c2.rates4(cr.temps, cr.scalebroad, precision=prec, q_begin=q0, q_end=q1)
+        t1 = time.perf_counter()
+        if i > 0:
+            e2e_times.append(t1 - t0)
+        h2d = 8 * (9 + cr.natoms * 4 + len(cr.temps)) + 96 * len(cr.fc2_idx) + 704 * len(cr.fc4_idx)
+        d2h = r.nbytes
+    e2e_s = float(np.mean(e2e_times))
+    if ws > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = cands_step / e2e_s
+
+    line = None
+    if rank == 0:
+        base = None
+        rel_err = None
+        if not args.no_cpu_baseline:
+            base, sel, ref = cpu_baseline(cr, args.cpu_sample_seconds, w, e, v)
+            gpu = out.view(nT, N * nb).cpu().numpy()[:, sel]
+            rel_err = float(np.max(np.abs(gpu - ref) / np.abs(ref)))
+            base.pop("seconds", None)
+        line = {
+            "metric": "four-phonon process-terms/s", "value": value, "unit": "process-terms/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "s_per_rate_set": total_ms / args.steps * 1e-3,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "f64" if prec == binding.FP_PREC_FP64 else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": synth.WORKLOAD_NAMES[args.workload], "precision": args.precision,
+                       "candidates_per_step": cands_step, "accepted_per_step": st["accepted"],
+                       "l2": "flushed between timed steps (256 MB write)", "tile": st["tile"],
+                       "parallelism": f"q-partition over {ws} GPU(s)"},
+            "rel_err_vs_oracle_sampled": rel_err,
+            "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved_tflops / peak, "traffic": None,
+                         "pipe": "fp64" if prec == binding.FP_PREC_FP64 else "fp32",
+                         "kernel_ms": kms, "flops_per_launch": flops_launch},
+            "cpu_baseline": base,
+            "e2e": {"value": e2e_value, "unit": "process-terms/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "s_per_rate_set": e2e_s},
+            "gpu_launches": 3 * args.steps,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,142 @@
+/*
+ * fourphonon.h -- C-ABI of libfourphonon: four-phonon RTA scattering rates on one GB300 GPU.
+ *
+ * The library computes, for every phonon mode lambda = (q, j) of a regular q-grid, the
+ * four-phonon part of the relaxation-time-approximation rate (paper: Sec. 2.2, Eq. tao0):
+ *
+ *   1/tau_lambda = (1/N) [ sum_{++} 1/2 Gamma++ + sum_{+-} 1/2 Gamma+- + sum_{--} 1/6 Gamma-- ]
+ *
+ * with Gamma from Eq. 4phgamma, the vertex V4 from Eq. V4 (r_j = cell vector of atom j),
+ * momentum q''' = q +- q' +- q'' (mod G) (Sec. 2.2, text of Eq. tao0), and the adaptive
+ * Gaussian delta of Sec. 2.4 / App. B, sigma = scalebroad |v'' - v'''| |dq|.
+ *
+ * Units: lengths in Angstrom, masses in amu, Phi2 in eV/A^2, Phi4 in eV/A^4, T in K,
+ * frequencies in rad/ps, velocities in A/ps, rates in 1/ps.
+ *
+ * Conventions shared by every call:
+ *   - grid index g = (g1 * N2 + g2) * N3 + g3, q_g = sum_a (g_a / N_a) b_a, b_a the reciprocal
+ *     vectors including 2 pi; mode index lambda = g * nb + j, nb = 3 * natoms; branches ascend in omega;
+ *   - eigenvector layout [g][j][3 * atom + alpha] as (re, im) double pairs;
+ *   - all host pointers are owned by the caller and only read (inputs) or written (outputs)
+ *     during the call; the library copies what it keeps;
+ *   - device memory is owned by the context; one context = one device + one CUDA stream;
+ *     a context is not thread-safe;
+ *   - every entry point returns FP_OK (0) or a negative FP_E* code; fp_last_error() then
+ *     holds a one-line message.  On FP_ECUDA the context should be freed.
+ */
+#ifndef FOURPHONON_H
+#define FOURPHONON_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FP_OK 0
+#define FP_EINVAL (-1)     /* invalid argument (sizes, indices, masses, temperatures ...) */
+#define FP_ENOMEM (-2)     /* device or host allocation failed */
+#define FP_ECUDA (-3)      /* a CUDA call failed */
+#define FP_EUNSTABLE (-4)  /* omega^2 < -1e-8 max(omega^2) away from the three Gamma acoustic modes */
+#define FP_ESTATE (-6)     /* call out of order (e.g. rates before modes) */
+
+#define FP_PREC_FP64 0  /* vertex, Gaussian and sums in FP64 (parity path, 1e-10 vs the FP64 definition) */
+#define FP_PREC_MIXED 1 /* vertex and Gaussian in FP32, window decisions exact, sums in FP64 */
+
+typedef struct fp_ctx fp_ctx;
+
+/* Harmonic pair block Phi2(0 i; R j), 3x3 row-major (alpha, beta), eV/A^2 (Sec. 2.3, Eq. PE). */
+typedef struct {
+  int i, j;
+  int Rj[3];  /* cell of atom j in lattice coordinates */
+  double fc[9];
+} fp_fc2;
+
+/* Fourth-order block Phi4(0 i; Rj j; Rk k; Rl l), 81 values row-major (alpha, beta, gamma, theta),
+ * eV/A^4 (Sec. 2.3, Eqs. PE and fourth-order IFCs); atom i lies in the home cell. */
+typedef struct {
+  int i, j, k, l;
+  int Rj[3], Rk[3], Rl[3];
+  double fc[81];
+} fp_fc4;
+
+/* Options of fp_rates4.  Zero-initialised fields take the defaults of fp_default_opts(). */
+typedef struct {
+  int precision;                   /* FP_PREC_FP64 (default) or FP_PREC_MIXED */
+  double window;                   /* a term enters when |dw| <= window * max(sigma, sigma_min); default 2 */
+  double sigma_min;                /* delta := 1 below this sigma (Sec. 2.4), rad/ps; default 1e-10 */
+  int dq_mode;                     /* 0: |dq| = (|det B|/N)^(1/3); 1: per-axis sqrt(sum_a ((dv.b_a)/N_a)^2/3) */
+  const unsigned char* mode_mask;  /* host, N*nb bytes, nonzero = compute this mode; NULL = all */
+  int q_begin, q_end;              /* q-points [q_begin, q_end) get rates (others 0); q_end <= 0 means N */
+  int block_j0;                    /* kernel tile: branches j per work item (must divide nb); 0 = auto */
+  int k1_tile;                     /* kernel tile: q' points per work item; 0 = auto */
+  int threads;                     /* threads per block; 0 = auto */
+} fp_rates_opts;
+
+/* Counters of one fp_rates4 call. */
+typedef struct {
+  double candidates;   /* process terms examined: 3 * (selected modes) * N^2 * nb^3 */
+  double accepted[3];  /* terms inside the energy window for ++, +-, -- */
+  double flops;        /* vertex assembly + contraction flops issued (8 per complex multiply-add) */
+  double ms;           /* device time of the rate kernels (CUDA events on the context stream) */
+  int tile[4];         /* block_j0, k1_tile, threads, CTAs launched */
+} fp_stats;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int fp_version(void);
+
+/* Fill *opts with the defaults described in fp_rates_opts. */
+void fp_default_opts(fp_rates_opts* opts);
+
+/*
+ * Create a context on `device` and upload the crystal: lattice rows a1..a3 (A), natoms fractional
+ * positions (natoms x 3, informational: phases use cell vectors, Eq. V4), masses (amu, > 0), the
+ * Phi2 pair list and the Phi4 quartet list, and the q-grid (each N_a >= 1).  Indices must lie in
+ * [0, natoms).  On success *out owns all device memory of the problem; free it with fp_free().
+ */
+int fp_init(fp_ctx** out, const double lattice[9], int natoms, const double* frac_pos, const double* mass,
+            int n_fc2, const fp_fc2* fc2, int n_fc4, const fp_fc4* fc4, const int grid[3], int device);
+
+/* Use an existing CUDA stream (a cudaStream_t passed as void*) for all later work; NULL = the
+ * context's own stream.  The caller keeps the stream alive while the context uses it. */
+int fp_set_stream(fp_ctx* ctx, void* stream);
+
+/*
+ * Harmonic modes on the grid on the GPU (paper Sec. 2.1 harmonic step; velocities for Sec. 2.4):
+ * omega (N x nb), evec (N x nb x nb x 2), vel (N x nb x 3); each output may be NULL.
+ * Time reversal is exact (omega(-q) = omega(q), e(-q) = conj e(q), v(-q) = -v(q)), e is real and v = 0
+ * at self-conjugate q, the three Gamma acoustic modes have omega = 0, velocities are averaged over
+ * degenerate sets.  Returns FP_EUNSTABLE for imaginary frequencies.
+ */
+int fp_modes(fp_ctx* ctx, double* omega, double* evec, double* vel);
+
+/*
+ * Replace the modes by caller-supplied tables (same layouts as fp_modes).  The tables must obey
+ * exact time reversal as described for fp_modes (checked bitwise; FP_EINVAL otherwise); omega must
+ * be >= 0 and finite.
+ */
+int fp_set_modes(fp_ctx* ctx, const double* omega, const double* evec, const double* vel);
+
+/*
+ * Four-phonon RTA rates (Eqs. tao0, 4phgamma, V4; Sec. 2.4) at nT temperatures T (K, > 0) with
+ * broadening scale `scalebroad` (> 0).  rates: host, nT x N x nb, ps^-1, written in full (modes not
+ * selected by the mask / q-range, and zero-frequency modes, get 0).  opts and stats may be NULL.
+ * Requires fp_modes or fp_set_modes first (FP_ESTATE otherwise).
+ */
+int fp_rates4(fp_ctx* ctx, int nT, const double* T, double scalebroad, const fp_rates_opts* opts,
+              double* rates, fp_stats* stats);
+
+/* As fp_rates4, but `d_rates` is a device pointer (nT x N x nb doubles) on the context's device;
+ * the call returns after the work is complete on the context stream. */
+int fp_rates4_device(fp_ctx* ctx, int nT, const double* T, double scalebroad, const fp_rates_opts* opts,
+                     double* d_rates, fp_stats* stats);
+
+/* Release the context and all its device memory.  NULL is ignored. */
+void fp_free(fp_ctx* ctx);
+
+/* Message of the last failed call on ctx (or of the last failed fp_init when ctx is NULL). */
+const char* fp_last_error(const fp_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FOURPHONON_H */

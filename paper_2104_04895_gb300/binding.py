@@ -1,0 +1,232 @@
+"""Thin ctypes binding of libfourphonon (same names as include/fourphonon.h).
+
+Argument marshalling only: every step of the rate path runs in the library's CUDA
+kernels.  Loading fails loudly when the library has not been built; there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FP_OK = 0
+FP_EINVAL = -1
+FP_ENOMEM = -2
+FP_ECUDA = -3
+FP_EUNSTABLE = -4
+FP_ESTATE = -6
+FP_PREC_FP64 = 0
+FP_PREC_MIXED = 1
+
+
+class fp_fc2(ctypes.Structure):
+    _fields_ = [("i", ctypes.c_int), ("j", ctypes.c_int), ("Rj", ctypes.c_int * 3), ("fc", ctypes.c_double * 9)]
+
+
+class fp_fc4(ctypes.Structure):
+    _fields_ = [("i", ctypes.c_int), ("j", ctypes.c_int), ("k", ctypes.c_int), ("l", ctypes.c_int),
+                ("Rj", ctypes.c_int * 3), ("Rk", ctypes.c_int * 3), ("Rl", ctypes.c_int * 3),
+                ("fc", ctypes.c_double * 81)]
+
+
+class fp_rates_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("window", ctypes.c_double), ("sigma_min", ctypes.c_double),
+                ("dq_mode", ctypes.c_int), ("mode_mask", ctypes.POINTER(ctypes.c_ubyte)),
+                ("q_begin", ctypes.c_int), ("q_end", ctypes.c_int), ("block_j0", ctypes.c_int),
+                ("k1_tile", ctypes.c_int), ("threads", ctypes.c_int)]
+
+
+class fp_stats(ctypes.Structure):
+    _fields_ = [("candidates", ctypes.c_double), ("accepted", ctypes.c_double * 3), ("flops", ctypes.c_double),
+                ("ms", ctypes.c_double), ("tile", ctypes.c_int * 4)]
+
+    def as_dict(self):
+        return {"candidates": self.candidates, "accepted": list(self.accepted), "flops": self.flops,
+                "ms": self.ms, "tile": list(self.tile)}
+
+
+EXPORTS = ["fp_version", "fp_default_opts", "fp_init", "fp_set_stream", "fp_modes", "fp_set_modes", "fp_rates4",
+           "fp_rates4_device", "fp_free", "fp_last_error"]
+
+_LIB = None
+
+
+class FourPhononError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libfourphonon error {code}: {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libfourphonon.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or library_path()
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"libfourphonon.so is not built ({path}); run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.fp_version.restype = ctypes.c_int
+    L.fp_default_opts.argtypes = [ctypes.POINTER(fp_rates_opts)]
+    L.fp_default_opts.restype = None
+    L.fp_init.argtypes = [ctypes.POINTER(vp), dp, ctypes.c_int, dp, dp, ctypes.c_int, ctypes.POINTER(fp_fc2),
+                          ctypes.c_int, ctypes.POINTER(fp_fc4), ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+    L.fp_init.restype = ctypes.c_int
+    L.fp_set_stream.argtypes = [vp, vp]
+    L.fp_set_stream.restype = ctypes.c_int
+    L.fp_modes.argtypes = [vp, vp, vp, vp]
+    L.fp_modes.restype = ctypes.c_int
+    L.fp_set_modes.argtypes = [vp, dp, dp, dp]
+    L.fp_set_modes.restype = ctypes.c_int
+    L.fp_rates4.argtypes = [vp, ctypes.c_int, dp, ctypes.c_double, ctypes.POINTER(fp_rates_opts), dp,
+                            ctypes.POINTER(fp_stats)]
+    L.fp_rates4.restype = ctypes.c_int
+    L.fp_rates4_device.argtypes = [vp, ctypes.c_int, dp, ctypes.c_double, ctypes.POINTER(fp_rates_opts), vp,
+                                   ctypes.POINTER(fp_stats)]
+    L.fp_rates4_device.restype = ctypes.c_int
+    L.fp_free.argtypes = [vp]
+    L.fp_free.restype = None
+    L.fp_last_error.argtypes = [vp]
+    L.fp_last_error.restype = ctypes.c_char_p
+    _LIB = L
+    return L
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(L, ctx, rc):
+    if rc != FP_OK:
+        msg = L.fp_last_error(ctx)
+        raise FourPhononError(rc, msg.decode() if msg else "")
+
+
+def pack_fc2(idx, val):
+    arr = (fp_fc2 * max(1, len(idx)))()
+    for b, (ix, v) in enumerate(zip(idx, val)):
+        arr[b].i, arr[b].j = int(ix[0]), int(ix[1])
+        for d in range(3):
+            arr[b].Rj[d] = int(ix[2 + d])
+        ctypes.memmove(arr[b].fc, np.ascontiguousarray(v, np.float64).ctypes.data, 72)
+    return arr
+
+
+def pack_fc4(idx, val):
+    arr = (fp_fc4 * max(1, len(idx)))()
+    for b, (ix, v) in enumerate(zip(idx, val)):
+        arr[b].i, arr[b].j, arr[b].k, arr[b].l = (int(x) for x in ix[:4])
+        for d in range(3):
+            arr[b].Rj[d] = int(ix[4 + d])
+            arr[b].Rk[d] = int(ix[7 + d])
+            arr[b].Rl[d] = int(ix[10 + d])
+        ctypes.memmove(arr[b].fc, np.ascontiguousarray(v, np.float64).ctypes.data, 648)
+    return arr
+
+
+class Context:
+    """One fp_ctx: a crystal, its q-grid and its device memory."""
+
+    def __init__(self, lattice, frac, mass, fc2_idx, fc2_val, fc4_idx, fc4_val, grid, device=0):
+        self.L = load()
+        self.nb = 3 * len(mass)
+        self.grid = tuple(int(g) for g in grid)
+        self.N = int(np.prod(self.grid))
+        lat = np.ascontiguousarray(lattice, np.float64).reshape(9)
+        fr = np.ascontiguousarray(frac, np.float64).reshape(-1)
+        m = np.ascontiguousarray(mass, np.float64)
+        g = (ctypes.c_int * 3)(*self.grid)
+        f2 = pack_fc2(fc2_idx, fc2_val)
+        f4 = pack_fc4(fc4_idx, fc4_val)
+        h = ctypes.c_void_p()
+        rc = self.L.fp_init(ctypes.byref(h), _dp(lat), len(m), _dp(fr), _dp(m), len(fc2_idx), f2, len(fc4_idx), f4,
+                            g, int(device))
+        _check(self.L, None, rc)
+        self.h = h
+
+    @classmethod
+    def from_crystal(cls, cr, device=0):
+        return cls(cr.lattice, cr.frac, cr.mass, cr.fc2_idx, cr.fc2_val, cr.fc4_idx, cr.fc4_val, cr.grid, device)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.fp_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_stream(self, stream_handle: int | None):
+        _check(self.L, self.h, self.L.fp_set_stream(self.h, ctypes.c_void_p(stream_handle or 0)))
+
+    def modes(self, copy=True):
+        if not copy:
+            _check(self.L, self.h, self.L.fp_modes(self.h, None, None, None))
+            return None
+        om = np.zeros((self.N, self.nb))
+        ev = np.zeros((self.N, self.nb, self.nb, 2))
+        ve = np.zeros((self.N, self.nb, 3))
+        rc = self.L.fp_modes(self.h, om.ctypes.data, ev.ctypes.data, ve.ctypes.data)
+        _check(self.L, self.h, rc)
+        return om, ev[..., 0] + 1j * ev[..., 1], ve
+
+    def set_modes(self, omega, evec, vel):
+        om = np.ascontiguousarray(omega, np.float64)
+        if np.iscomplexobj(evec):
+            ev = np.ascontiguousarray(np.stack([evec.real, evec.imag], axis=-1))
+        else:
+            ev = np.ascontiguousarray(evec, np.float64)
+        ve = np.ascontiguousarray(vel, np.float64)
+        _check(self.L, self.h, self.L.fp_set_modes(self.h, _dp(om), _dp(ev), _dp(ve)))
+
+    @staticmethod
+    def make_opts(precision=FP_PREC_FP64, window=2.0, sigma_min=1e-10, dq_mode=0, mode_mask=None, q_begin=0,
+                  q_end=0, block_j0=0, k1_tile=0, threads=0):
+        o = fp_rates_opts()
+        o.precision, o.window, o.sigma_min, o.dq_mode = int(precision), float(window), float(sigma_min), int(dq_mode)
+        o.q_begin, o.q_end, o.block_j0, o.k1_tile, o.threads = int(q_begin), int(q_end), int(block_j0), \
+            int(k1_tile), int(threads)
+        keep = None
+        if mode_mask is not None:
+            keep = np.ascontiguousarray(mode_mask, np.uint8)
+            o.mode_mask = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
+        return o, keep
+
+    def rates4(self, temps, scalebroad=1.0, **opts):
+        T = np.ascontiguousarray(temps, np.float64).reshape(-1)
+        o, keep = self.make_opts(**opts)
+        out = np.zeros((len(T), self.N, self.nb))
+        st = fp_stats()
+        rc = self.L.fp_rates4(self.h, len(T), _dp(T), float(scalebroad), ctypes.byref(o), _dp(out), ctypes.byref(st))
+        _check(self.L, self.h, rc)
+        del keep
+        return out, st.as_dict()
+
+    def rates4_device(self, temps, d_rates_ptr: int, scalebroad=1.0, **opts):
+        T = np.ascontiguousarray(temps, np.float64).reshape(-1)
+        o, keep = self.make_opts(**opts)
+        st = fp_stats()
+        rc = self.L.fp_rates4_device(self.h, len(T), _dp(T), float(scalebroad), ctypes.byref(o),
+                                     ctypes.c_void_p(d_rates_ptr), ctypes.byref(st))
+        _check(self.L, self.h, rc)
+        del keep
+        return st.as_dict()

@@ -1,0 +1,563 @@
+// C-ABI of libfourphonon: context, validation, device memory, launches (see include/fourphonon.h).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <tuple>
+
+#include "fp_internal.cuh"
+
+namespace {
+
+std::string g_init_error;
+
+int fail(fp_ctx* c, int code, const std::string& msg) {
+  if (c)
+    c->err = msg;
+  else
+    g_init_error = msg;
+  return code;
+}
+
+#define FP_CUDA(ctx, call)                                                                   \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail((ctx), e_ == cudaErrorMemoryAllocation ? FP_ENOMEM : FP_ECUDA,             \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  return cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+int gcd(int a, int b) { return b == 0 ? a : gcd(b, a % b); }
+
+void reciprocal(const double A[9], double B[9], double* det_out) {
+  double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+               A[2] * (A[3] * A[7] - A[4] * A[6]);
+  // rows b_a = 2 pi (A^{-1})^T rows: b_a[c] = 2 pi inv[c][a]; inv = adj / det
+  double adj[9] = {A[4] * A[8] - A[5] * A[7], A[2] * A[7] - A[1] * A[8], A[1] * A[5] - A[2] * A[4],
+                   A[5] * A[6] - A[3] * A[8], A[0] * A[8] - A[2] * A[6], A[2] * A[3] - A[0] * A[5],
+                   A[3] * A[7] - A[4] * A[6], A[1] * A[6] - A[0] * A[7], A[0] * A[4] - A[1] * A[3]};
+  double inv[9];
+  for (int k = 0; k < 9; ++k) inv[k] = adj[k] / det;
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) B[3 * a + c] = 2.0 * fp::kPi * inv[3 * c + a];
+  if (det_out) *det_out = det;
+}
+
+double det3(const double M[9]) {
+  return M[0] * (M[4] * M[8] - M[5] * M[7]) - M[1] * (M[3] * M[8] - M[5] * M[6]) +
+         M[2] * (M[3] * M[7] - M[4] * M[6]);
+}
+
+int ensure_modes_buffers(fp_ctx* c) {
+  if (!c->d_omega) {
+    FP_CUDA(c, dalloc(&c->d_omega, (size_t)c->N * c->nb));
+    FP_CUDA(c, dalloc(&c->d_evec, (size_t)c->N * c->nb * c->nb));
+    FP_CUDA(c, dalloc(&c->d_vel, (size_t)c->N * c->nb * 3));
+  }
+  return FP_OK;
+}
+
+int grid_index(const fp_ctx* c, const int g[3]) { return (g[0] * c->grid[1] + g[1]) * c->grid[2] + g[2]; }
+
+int neg_index(const fp_ctx* c, int q) {
+  int g[3] = {q / (c->grid[1] * c->grid[2]), (q / c->grid[2]) % c->grid[1], q % c->grid[2]};
+  int m[3];
+  for (int d = 0; d < 3; ++d) m[d] = (c->grid[d] - g[d]) % c->grid[d];
+  return grid_index(c, m);
+}
+
+}  // namespace
+
+extern "C" {
+
+int fp_version(void) { return 10000; }
+
+void fp_default_opts(fp_rates_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = FP_PREC_FP64;
+  o->window = 2.0;
+  o->sigma_min = 1e-10;
+  o->dq_mode = 0;
+  o->mode_mask = nullptr;
+  o->q_begin = 0;
+  o->q_end = 0;
+}
+
+const char* fp_last_error(const fp_ctx* c) { return c ? c->err.c_str() : g_init_error.c_str(); }
+
+void fp_free(fp_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->own_stream) cudaStreamSynchronize(c->own_stream);
+  dfree(c->d_fc2_idx);
+  dfree(c->d_fc2_val);
+  dfree(c->d_mass);
+  dfree(c->d_qmeta);
+  dfree(c->d_qfc);
+  dfree(c->d_gmeta);
+  dfree(c->d_grp_qstart);
+  dfree(c->d_grp_q);
+  dfree(c->d_kl_start);
+  dfree(c->d_kl_grp);
+  dfree(c->d_tw);
+  dfree(c->d_omega);
+  dfree(c->d_evec);
+  dfree(c->d_vel);
+  dfree(c->d_flag);
+  dfree(c->d_wt);
+  dfree(c->d_partial);
+  dfree(c->d_counters);
+  dfree(c->d_T);
+  dfree(c->d_mask);
+  dfree(c->d_rates);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  delete c;
+}
+
+int fp_init(fp_ctx** out, const double lattice[9], int natoms, const double* frac_pos, const double* mass,
+            int n_fc2, const fp_fc2* fc2, int n_fc4, const fp_fc4* fc4, const int grid[3], int device) {
+  (void)frac_pos;
+  if (!out) return fail(nullptr, FP_EINVAL, "fp_init: out is NULL");
+  *out = nullptr;
+  if (!lattice || !mass || !grid) return fail(nullptr, FP_EINVAL, "fp_init: NULL lattice, mass or grid");
+  if (natoms < 1 || 3 * natoms > fp::kMaxNb)
+    return fail(nullptr, FP_EINVAL, "fp_init: natoms must be in [1, 4]");
+  for (int a = 0; a < 3; ++a)
+    if (grid[a] < 1 || grid[a] > 64) return fail(nullptr, FP_EINVAL, "fp_init: grid dimensions must be in [1, 64]");
+  for (int i = 0; i < 9; ++i)
+    if (!std::isfinite(lattice[i])) return fail(nullptr, FP_EINVAL, "fp_init: non-finite lattice");
+  if (std::fabs(det3(lattice)) < 1e-12) return fail(nullptr, FP_EINVAL, "fp_init: singular lattice");
+  for (int i = 0; i < natoms; ++i)
+    if (!(mass[i] > 0.0) || !std::isfinite(mass[i])) return fail(nullptr, FP_EINVAL, "fp_init: masses must be > 0");
+  if (n_fc2 < 0 || (n_fc2 > 0 && !fc2)) return fail(nullptr, FP_EINVAL, "fp_init: bad Phi2 list");
+  if (n_fc4 < 0 || (n_fc4 > 0 && !fc4)) return fail(nullptr, FP_EINVAL, "fp_init: bad Phi4 list");
+  for (int b = 0; b < n_fc2; ++b) {
+    if (fc2[b].i < 0 || fc2[b].i >= natoms || fc2[b].j < 0 || fc2[b].j >= natoms)
+      return fail(nullptr, FP_EINVAL, "fp_init: Phi2 atom index out of range");
+    for (int k = 0; k < 9; ++k)
+      if (!std::isfinite(fc2[b].fc[k])) return fail(nullptr, FP_EINVAL, "fp_init: non-finite Phi2");
+  }
+  for (int b = 0; b < n_fc4; ++b) {
+    const fp_fc4& f = fc4[b];
+    int at[4] = {f.i, f.j, f.k, f.l};
+    for (int k = 0; k < 4; ++k)
+      if (at[k] < 0 || at[k] >= natoms) return fail(nullptr, FP_EINVAL, "fp_init: Phi4 atom index out of range");
+    for (int k = 0; k < 81; ++k)
+      if (!std::isfinite(f.fc[k])) return fail(nullptr, FP_EINVAL, "fp_init: non-finite Phi4");
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+    return fail(nullptr, FP_ECUDA, "fp_init: no CUDA device");
+  if (device < 0 || device >= ndev) return fail(nullptr, FP_EINVAL, "fp_init: bad device ordinal");
+
+  fp_ctx* c = new fp_ctx();
+  c->device = device;
+  c->natoms = natoms;
+  c->nb = 3 * natoms;
+  for (int a = 0; a < 3; ++a) c->grid[a] = grid[a];
+  c->N = grid[0] * grid[1] * grid[2];
+  int L = 1;
+  for (int a = 0; a < 3; ++a) L = L / gcd(L, grid[a]) * grid[a];
+  c->L = L;
+  std::memcpy(c->lattice, lattice, sizeof(c->lattice));
+  reciprocal(lattice, c->rec, nullptr);
+  c->mass.assign(mass, mass + natoms);
+
+  auto bail = [&](int rc) {
+    g_init_error = c->err;
+    fp_free(c);
+    return rc;
+  };
+#define INIT_CUDA(call)                                                                               \
+  do {                                                                                                \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess)                                                                            \
+      return bail(fail(c, e_ == cudaErrorMemoryAllocation ? FP_ENOMEM : FP_ECUDA,                     \
+                       std::string(#call) + ": " + cudaGetErrorString(e_)));                          \
+  } while (0)
+
+  INIT_CUDA(cudaSetDevice(device));
+  INIT_CUDA(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
+  c->stream = c->own_stream;
+  INIT_CUDA(cudaEventCreate(&c->ev0));
+  INIT_CUDA(cudaEventCreate(&c->ev1));
+  cudaStream_t s = c->stream;
+
+  // harmonic pairs
+  c->n_fc2 = n_fc2;
+  std::vector<int> idx2(5 * (size_t)n_fc2);
+  std::vector<double> val2(9 * (size_t)n_fc2);
+  for (int b = 0; b < n_fc2; ++b) {
+    idx2[5 * b] = fc2[b].i;
+    idx2[5 * b + 1] = fc2[b].j;
+    for (int d = 0; d < 3; ++d) idx2[5 * b + 2 + d] = fc2[b].Rj[d];
+    for (int k = 0; k < 9; ++k) val2[9 * b + k] = fc2[b].fc[k];
+  }
+  INIT_CUDA(dalloc(&c->d_fc2_idx, idx2.size()));
+  INIT_CUDA(dalloc(&c->d_fc2_val, val2.size()));
+  INIT_CUDA(dalloc(&c->d_mass, (size_t)natoms));
+  INIT_CUDA(cudaMemcpyAsync(c->d_fc2_idx, idx2.data(), idx2.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  INIT_CUDA(cudaMemcpyAsync(c->d_fc2_val, val2.data(), val2.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  INIT_CUDA(cudaMemcpyAsync(c->d_mass, mass, natoms * sizeof(double), cudaMemcpyHostToDevice, s));
+
+  // quartets grouped by (atom k, atom l, D = R_k - R_l)
+  c->nquart = n_fc4;
+  std::map<std::tuple<int, int, int, int, int>, int> gid;
+  std::vector<int> qgroup(n_fc4);
+  for (int b = 0; b < n_fc4; ++b) {
+    const fp_fc4& f = fc4[b];
+    auto key = std::make_tuple(f.k, f.l, f.Rk[0] - f.Rl[0], f.Rk[1] - f.Rl[1], f.Rk[2] - f.Rl[2]);
+    auto it = gid.find(key);
+    if (it == gid.end()) it = gid.emplace(key, 0).first;
+    (void)it;
+  }
+  {
+    int n = 0;
+    for (auto& kv : gid) kv.second = n++;  // sorted order: by (k, l, D)
+  }
+  c->G = (int)gid.size();
+  std::vector<int> gmeta(5 * (size_t)c->G);
+  for (auto& kv : gid) {
+    int gi = kv.second;
+    gmeta[5 * gi] = std::get<0>(kv.first);
+    gmeta[5 * gi + 1] = std::get<1>(kv.first);
+    gmeta[5 * gi + 2] = std::get<2>(kv.first);
+    gmeta[5 * gi + 3] = std::get<3>(kv.first);
+    gmeta[5 * gi + 4] = std::get<4>(kv.first);
+  }
+  std::vector<int> qmeta(9 * (size_t)n_fc4), atoms4(4 * (size_t)n_fc4);
+  std::vector<double> qfc(81 * (size_t)n_fc4);
+  for (int b = 0; b < n_fc4; ++b) {
+    const fp_fc4& f = fc4[b];
+    auto key = std::make_tuple(f.k, f.l, f.Rk[0] - f.Rl[0], f.Rk[1] - f.Rl[1], f.Rk[2] - f.Rl[2]);
+    qgroup[b] = gid[key];
+    qmeta[9 * b] = f.i;
+    qmeta[9 * b + 1] = f.j;
+    qmeta[9 * b + 2] = qgroup[b];
+    for (int d = 0; d < 3; ++d) {
+      qmeta[9 * b + 3 + d] = f.Rj[d];
+      qmeta[9 * b + 6 + d] = f.Rl[d];
+    }
+    atoms4[4 * b] = f.i;
+    atoms4[4 * b + 1] = f.j;
+    atoms4[4 * b + 2] = f.k;
+    atoms4[4 * b + 3] = f.l;
+    std::memcpy(&qfc[81 * (size_t)b], f.fc, 81 * sizeof(double));
+  }
+  std::vector<int> grp_qstart(c->G + 1, 0), grp_q(n_fc4);
+  for (int b = 0; b < n_fc4; ++b) grp_qstart[qgroup[b] + 1]++;
+  for (int gi = 0; gi < c->G; ++gi) grp_qstart[gi + 1] += grp_qstart[gi];
+  {
+    std::vector<int> fill(grp_qstart.begin(), grp_qstart.end() - 1);
+    for (int b = 0; b < n_fc4; ++b) grp_q[fill[qgroup[b]]++] = b;
+  }
+  const int na2 = natoms * natoms;
+  std::vector<int> kl_start(na2 + 1, 0), kl_grp(c->G);
+  for (int gi = 0; gi < c->G; ++gi) kl_start[gmeta[5 * gi] * natoms + gmeta[5 * gi + 1] + 1]++;
+  for (int k = 0; k < na2; ++k) kl_start[k + 1] += kl_start[k];
+  {
+    std::vector<int> fill(kl_start.begin(), kl_start.end() - 1);
+    for (int gi = 0; gi < c->G; ++gi) kl_grp[fill[gmeta[5 * gi] * natoms + gmeta[5 * gi + 1]]++] = gi;
+  }
+  int* d_atoms4 = nullptr;
+  INIT_CUDA(dalloc(&c->d_qmeta, qmeta.size()));
+  INIT_CUDA(dalloc(&c->d_qfc, qfc.size()));
+  INIT_CUDA(dalloc(&c->d_gmeta, gmeta.size()));
+  INIT_CUDA(dalloc(&c->d_grp_qstart, grp_qstart.size()));
+  INIT_CUDA(dalloc(&c->d_grp_q, grp_q.size()));
+  INIT_CUDA(dalloc(&c->d_kl_start, kl_start.size()));
+  INIT_CUDA(dalloc(&c->d_kl_grp, kl_grp.size()));
+  INIT_CUDA(dalloc(&d_atoms4, atoms4.size()));
+  INIT_CUDA(cudaMemcpyAsync(c->d_qmeta, qmeta.data(), qmeta.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  INIT_CUDA(cudaMemcpyAsync(c->d_qfc, qfc.data(), qfc.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  INIT_CUDA(cudaMemcpyAsync(c->d_gmeta, gmeta.data(), gmeta.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  INIT_CUDA(cudaMemcpyAsync(c->d_grp_qstart, grp_qstart.data(), grp_qstart.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, s));
+  INIT_CUDA(cudaMemcpyAsync(c->d_grp_q, grp_q.data(), grp_q.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  INIT_CUDA(cudaMemcpyAsync(c->d_kl_start, kl_start.data(), kl_start.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  INIT_CUDA(cudaMemcpyAsync(c->d_kl_grp, kl_grp.data(), kl_grp.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  INIT_CUDA(cudaMemcpyAsync(d_atoms4, atoms4.data(), atoms4.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  INIT_CUDA(fp::launch_scale_fc4(c->d_qfc, d_atoms4, c->d_mass, n_fc4, s));
+  INIT_CUDA(dalloc(&c->d_tw, (size_t)c->L));
+  INIT_CUDA(fp::launch_twiddles(c, s));
+  INIT_CUDA(dalloc(&c->d_flag, 1));
+  INIT_CUDA(dalloc(&c->d_counters, 4));
+  INIT_CUDA(cudaStreamSynchronize(s));
+  cudaFree(d_atoms4);
+#undef INIT_CUDA
+  *out = c;
+  return FP_OK;
+}
+
+int fp_set_stream(fp_ctx* c, void* stream) {
+  if (!c) return fail(nullptr, FP_EINVAL, "fp_set_stream: NULL context");
+  c->stream = stream ? reinterpret_cast<cudaStream_t>(stream) : c->own_stream;
+  return FP_OK;
+}
+
+int fp_modes(fp_ctx* c, double* omega, double* evec, double* vel) {
+  if (!c) return fail(nullptr, FP_EINVAL, "fp_modes: NULL context");
+  FP_CUDA(c, cudaSetDevice(c->device));
+  int rc = ensure_modes_buffers(c);
+  if (rc) return rc;
+  cudaStream_t s = c->stream;
+  FP_CUDA(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
+  FP_CUDA(c, fp::launch_modes(c, s));
+  int flag = 0;
+  FP_CUDA(c, cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  const size_t nm = (size_t)c->N * c->nb;
+  if (omega) FP_CUDA(c, cudaMemcpyAsync(omega, c->d_omega, nm * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (evec) FP_CUDA(c, cudaMemcpyAsync(evec, c->d_evec, nm * c->nb * sizeof(double2), cudaMemcpyDeviceToHost, s));
+  if (vel) FP_CUDA(c, cudaMemcpyAsync(vel, c->d_vel, nm * 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  FP_CUDA(c, cudaStreamSynchronize(s));
+  if (flag) {
+    c->have_modes = false;
+    return fail(c, FP_EUNSTABLE, "fp_modes: imaginary frequencies (omega^2 < -1e-8 max omega^2)");
+  }
+  c->have_modes = true;
+  return FP_OK;
+}
+
+int fp_set_modes(fp_ctx* c, const double* omega, const double* evec, const double* vel) {
+  if (!c) return fail(nullptr, FP_EINVAL, "fp_set_modes: NULL context");
+  if (!omega || !evec || !vel) return fail(c, FP_EINVAL, "fp_set_modes: NULL table");
+  const int nb = c->nb;
+  for (int q = 0; q < c->N; ++q) {
+    const int p = neg_index(c, q);
+    for (int j = 0; j < nb; ++j) {
+      double w = omega[q * nb + j];
+      if (!(w >= 0.0) || !std::isfinite(w)) return fail(c, FP_EINVAL, "fp_set_modes: omega must be finite and >= 0");
+      if (omega[p * nb + j] != w) return fail(c, FP_EINVAL, "fp_set_modes: omega(-q) != omega(q)");
+      for (int d = 0; d < 3; ++d)
+        if (vel[(q * nb + j) * 3 + d] != -vel[(p * nb + j) * 3 + d])
+          return fail(c, FP_EINVAL, "fp_set_modes: v(-q) != -v(q)");
+      for (int k = 0; k < nb; ++k) {
+        const double* a = evec + 2 * (((size_t)q * nb + j) * nb + k);
+        const double* b = evec + 2 * (((size_t)p * nb + j) * nb + k);
+        if (a[0] != b[0] || a[1] != -b[1]) return fail(c, FP_EINVAL, "fp_set_modes: e(-q) != conj e(q)");
+      }
+    }
+  }
+  FP_CUDA(c, cudaSetDevice(c->device));
+  int rc = ensure_modes_buffers(c);
+  if (rc) return rc;
+  const size_t nm = (size_t)c->N * nb;
+  cudaStream_t s = c->stream;
+  FP_CUDA(c, cudaMemcpyAsync(c->d_omega, omega, nm * sizeof(double), cudaMemcpyHostToDevice, s));
+  FP_CUDA(c, cudaMemcpyAsync(c->d_evec, evec, nm * nb * sizeof(double2), cudaMemcpyHostToDevice, s));
+  FP_CUDA(c, cudaMemcpyAsync(c->d_vel, vel, nm * 3 * sizeof(double), cudaMemcpyHostToDevice, s));
+  FP_CUDA(c, cudaStreamSynchronize(s));
+  c->have_modes = true;
+  return FP_OK;
+}
+
+static int rates_impl(fp_ctx* c, int nT, const double* T, double sb, const fp_rates_opts* user, double* d_out,
+                      fp_stats* stats) {
+  fp_rates_opts o;
+  fp_default_opts(&o);
+  if (user) {
+    o = *user;
+    if (o.window == 0.0) o.window = 2.0;
+    if (o.sigma_min == 0.0) o.sigma_min = 1e-10;
+  }
+  if (!c->have_modes) return fail(c, FP_ESTATE, "fp_rates4: call fp_modes or fp_set_modes first");
+  if (nT < 1 || nT > fp::kMaxT || !T) return fail(c, FP_EINVAL, "fp_rates4: nT must be in [1, 16]");
+  for (int i = 0; i < nT; ++i)
+    if (!(T[i] > 0.0) || !std::isfinite(T[i])) return fail(c, FP_EINVAL, "fp_rates4: temperatures must be > 0");
+  if (!(sb > 0.0) || !std::isfinite(sb)) return fail(c, FP_EINVAL, "fp_rates4: scalebroad must be > 0");
+  if (!(o.window > 0.0) || !(o.sigma_min > 0.0)) return fail(c, FP_EINVAL, "fp_rates4: window, sigma_min > 0");
+  if (o.precision != FP_PREC_FP64 && o.precision != FP_PREC_MIXED)
+    return fail(c, FP_EINVAL, "fp_rates4: unknown precision");
+  if (o.dq_mode != 0 && o.dq_mode != 1) return fail(c, FP_EINVAL, "fp_rates4: dq_mode must be 0 or 1");
+  const int N = c->N, nb = c->nb;
+  const int q_end = o.q_end <= 0 ? N : o.q_end;
+  if (o.q_begin < 0 || o.q_begin > q_end || q_end > N) return fail(c, FP_EINVAL, "fp_rates4: bad q range");
+  const int nq_sel = q_end - o.q_begin;
+
+  // tiles
+  int J = o.block_j0;
+  if (J <= 0) {
+    J = nb;
+    while (J > 1 && fp::rates_smem_bytes(o.precision, nb, J, c->G, c->nquart, nT, 384) > 112 * 1024) {
+      int nj = J - 1;
+      while (nj > 1 && nb % nj) --nj;
+      J = nj;
+    }
+  }
+  if (J < 1 || nb % J) return fail(c, FP_EINVAL, "fp_rates4: block_j0 must divide nb");
+  int threads = o.threads;
+  if (threads <= 0) {
+    threads = 32 * J;
+    while (threads < 160) threads += 32 * J;
+  }
+  if (threads % (32 * J) || threads > 384) return fail(c, FP_EINVAL, "fp_rates4: threads must be a multiple of 32*block_j0, <= 384");
+  int t1 = o.k1_tile > 0 ? o.k1_tile : (N + 511) / 512;
+  const int nchunk = nb / J;
+  const int ntile = (N + t1 - 1) / t1;
+  const long long n_items = (long long)ntile * nq_sel * nchunk;
+  const size_t smem = fp::rates_smem_bytes(o.precision, nb, J, c->G, c->nquart, nT, threads);
+  if (smem > 227 * 1024) return fail(c, FP_EINVAL, "fp_rates4: tile does not fit in shared memory");
+
+  FP_CUDA(c, cudaSetDevice(c->device));
+  cudaStream_t s = c->stream;
+  const size_t nm = (size_t)N * nb;
+  // scratch
+  size_t wt_need = 3 * nm * nT;
+  if (c->wt_cap < wt_need) {
+    dfree(c->d_wt);
+    c->wt_cap = 0;
+    FP_CUDA(c, dalloc(&c->d_wt, wt_need));
+    c->wt_cap = wt_need;
+  }
+  size_t part_need = (size_t)n_items * J * nT;
+  if (c->partial_cap < part_need) {
+    dfree(c->d_partial);
+    c->partial_cap = 0;
+    FP_CUDA(c, dalloc(&c->d_partial, part_need));
+    c->partial_cap = part_need;
+  }
+  if (!c->d_T) FP_CUDA(c, dalloc(&c->d_T, (size_t)fp::kMaxT));
+  FP_CUDA(c, cudaMemcpyAsync(c->d_T, T, nT * sizeof(double), cudaMemcpyHostToDevice, s));
+  const unsigned char* d_mask = nullptr;
+  if (o.mode_mask) {
+    if (!c->d_mask) FP_CUDA(c, dalloc(&c->d_mask, nm));
+    FP_CUDA(c, cudaMemcpyAsync(c->d_mask, o.mode_mask, nm, cudaMemcpyHostToDevice, s));
+    d_mask = c->d_mask;
+  }
+  FP_CUDA(c, fp::launch_weights(c, nT, c->d_T, c->d_wt, s));
+
+  fp::RatesArgs a;
+  a.N = N;
+  a.nb = nb;
+  a.natoms = c->natoms;
+  a.nT = nT;
+  a.L = c->L;
+  a.G = c->G;
+  a.nquart = c->nquart;
+  for (int d = 0; d < 3; ++d) {
+    a.grid[d] = c->grid[d];
+    a.Lfac[d] = c->L / c->grid[d];
+  }
+  a.J = J;
+  a.t1 = t1;
+  a.nchunk = nchunk;
+  a.ntile = ntile;
+  a.q_begin = o.q_begin;
+  a.nq_sel = nq_sel;
+  a.n_items = n_items;
+  a.omega = c->d_omega;
+  a.evec = c->d_evec;
+  a.vel = c->d_vel;
+  a.wt = c->d_wt;
+  a.qmeta = c->d_qmeta;
+  a.qfc = c->d_qfc;
+  a.gmeta = c->d_gmeta;
+  a.grp_qstart = c->d_grp_qstart;
+  a.grp_q = c->d_grp_q;
+  a.kl_start = c->d_kl_start;
+  a.kl_grp = c->d_kl_grp;
+  a.tw = c->d_tw;
+  a.mask = d_mask;
+  a.sb = sb;
+  a.window = o.window;
+  a.sigma_min = o.sigma_min;
+  double B[9], detA;
+  reciprocal(c->lattice, B, &detA);
+  a.dq = std::cbrt(std::fabs(det3(B)) / (double)N);
+  a.dq_mode = o.dq_mode;
+  for (int i = 0; i < 9; ++i) a.rec[i] = B[i];
+  a.partial = c->d_partial;
+  a.counter = c->d_counters;
+  a.counts = c->d_counters + 1;
+
+  int per_sm = fp::rates_max_ctas_per_sm(o.precision, threads, smem);
+  if (per_sm < 1) return fail(c, FP_EINVAL, "fp_rates4: kernel tile cannot be resident on an SM");
+  int nsm = 0;
+  FP_CUDA(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+  long long ctas = (long long)nsm * per_sm;
+  if (ctas > n_items) ctas = n_items > 0 ? n_items : 1;
+
+  FP_CUDA(c, cudaMemsetAsync(c->d_counters, 0, 4 * sizeof(unsigned long long), s));
+  FP_CUDA(c, cudaMemsetAsync(d_out, 0, (size_t)nT * nm * sizeof(double), s));
+  const double conv = fp::kConv;
+  const double pref = fp::kPi * fp::kHbar * fp::kHbar * conv * conv * conv * conv / (8.0 * (double)N * (double)N);
+  FP_CUDA(c, cudaEventRecord(c->ev0, s));
+  if (n_items > 0) {
+    FP_CUDA(c, fp::launch_rates(a, o.precision, threads, (int)ctas, smem, s));
+    FP_CUDA(c, fp::launch_reduce(a, pref, d_out, q_end, s));
+  }
+  FP_CUDA(c, cudaEventRecord(c->ev1, s));
+  unsigned long long counts[4] = {0, 0, 0, 0};
+  FP_CUDA(c, cudaMemcpyAsync(counts, c->d_counters, sizeof(counts), cudaMemcpyDeviceToHost, s));
+  FP_CUDA(c, cudaStreamSynchronize(s));
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    double nsel = 0;
+    if (o.mode_mask) {
+      for (int q = o.q_begin; q < q_end; ++q)
+        for (int j = 0; j < nb; ++j) nsel += o.mode_mask[(size_t)q * nb + j] ? 1 : 0;
+    } else {
+      nsel = (double)nq_sel * nb;
+    }
+    stats->candidates = 3.0 * nsel * (double)N * (double)N * (double)nb * nb * nb;
+    for (int p = 0; p < 3; ++p) stats->accepted[p] = (double)counts[1 + p];
+    const double pairs = 0.5 * (double)N * (double)(N + 1);
+    const double per_pair = 8.0 * (9.0 * J * nb * c->G + 2.0 * J * (double)nb * nb * nb * nb);
+    const double prolog = 8.0 * 9.0 * J * nb * 9.0 * c->nquart;
+    stats->flops = (double)nq_sel * nchunk * (pairs * per_pair + (double)N * prolog);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    stats->ms = ms;
+    stats->tile[0] = J;
+    stats->tile[1] = t1;
+    stats->tile[2] = threads;
+    stats->tile[3] = (int)ctas;
+  }
+  return FP_OK;
+}
+
+int fp_rates4_device(fp_ctx* c, int nT, const double* T, double scalebroad, const fp_rates_opts* opts,
+                     double* d_rates, fp_stats* stats) {
+  if (!c) return fail(nullptr, FP_EINVAL, "fp_rates4_device: NULL context");
+  if (!d_rates) return fail(c, FP_EINVAL, "fp_rates4_device: NULL output");
+  return rates_impl(c, nT, T, scalebroad, opts, d_rates, stats);
+}
+
+int fp_rates4(fp_ctx* c, int nT, const double* T, double scalebroad, const fp_rates_opts* opts, double* rates,
+              fp_stats* stats) {
+  if (!c) return fail(nullptr, FP_EINVAL, "fp_rates4: NULL context");
+  if (!rates) return fail(c, FP_EINVAL, "fp_rates4: NULL output");
+  if (nT < 1 || nT > fp::kMaxT) return fail(c, FP_EINVAL, "fp_rates4: nT must be in [1, 16]");
+  FP_CUDA(c, cudaSetDevice(c->device));
+  const size_t need = (size_t)nT * c->N * c->nb;
+  if (c->rates_cap < need) {
+    dfree(c->d_rates);
+    c->rates_cap = 0;
+    FP_CUDA(c, dalloc(&c->d_rates, need));
+    c->rates_cap = need;
+  }
+  int rc = rates_impl(c, nT, T, scalebroad, opts, c->d_rates, stats);
+  if (rc) return rc;
+  FP_CUDA(c, cudaMemcpyAsync(rates, c->d_rates, need * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  FP_CUDA(c, cudaStreamSynchronize(c->stream));
+  return FP_OK;
+}
+
+}  // extern "C"

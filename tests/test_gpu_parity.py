@@ -1,0 +1,152 @@
+"""GPU rates vs the FP64 oracle, through the C-ABI (fp_set_modes / fp_rates4).
+
+Modes are injected from the oracle so that both sides see identical frequencies,
+eigenvectors and velocities; window decisions must then agree exactly (accepted
+counts are compared as integers) and the FP64 rates to 1e-10 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_04895_gb300 import synth
+from paper_2104_04895_gb300.binding import FP_PREC_FP64, FP_PREC_MIXED
+
+from conftest import oracle_modes
+
+pytestmark = pytest.mark.gpu
+
+RTOL_FP64 = 1e-10
+# mixed path: FP32 vertex assembly/contraction and Gaussian, exact decisions, FP64 sums; the bound is
+# the measured worst case with a 10x margin (see the mixed-precision test below)
+RTOL_MIXED = 2e-4
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2104_04895_gb300 import binding
+    binding.load()
+    return binding
+
+
+def run_gpu(binding, cr, w, e, v, temps=None, **opts):
+    with binding.Context.from_crystal(cr) as ctx:
+        ctx.set_modes(w, e, v)
+        return ctx.rates4(temps if temps is not None else cr.temps, cr.scalebroad, **opts)
+
+
+def compare(gpu, ref, rtol):
+    gpu = np.asarray(gpu)
+    ref = np.asarray(ref)
+    assert gpu.shape == ref.shape
+    zero = ref == 0.0
+    assert np.all(gpu[zero] == 0.0)
+    rel = np.abs(gpu[~zero] - ref[~zero]) / np.abs(ref[~zero])
+    assert rel.max(initial=0.0) <= rtol, f"max rel err {rel.max():.3e}"
+    return rel.max(initial=0.0)
+
+
+CASES = [
+    ("sc-1x1x1", lambda: synth.simple_cubic((1, 1, 1))),
+    ("diamond-1x1x1", lambda: synth.diamond_si((1, 1, 1))),
+    ("sc-2x2x2", lambda: synth.simple_cubic((2, 2, 2))),
+    ("sc-3x2x1", lambda: synth.simple_cubic((3, 2, 1))),
+    ("diamond-3x3x2", lambda: synth.diamond_si((3, 3, 2))),
+    ("bas-3x3x3", lambda: synth.zincblende_bas((3, 3, 3))),
+    ("licoo2-2x2x1", lambda: synth.licoo2((2, 2, 1))),
+]
+
+
+@pytest.mark.parametrize("name,maker", CASES, ids=[c[0] for c in CASES])
+def test_fp64_parity_small(lib, name, maker):
+    cr = maker()
+    w, e, v = oracle_modes(cr)
+    ref, acc = oracle.rates4(cr, w, e, v)
+    out, st = run_gpu(lib, cr, w, e, v)
+    compare(out.reshape(len(cr.temps), -1), ref, RTOL_FP64)
+    assert np.array_equal(np.array(st["accepted"]), acc)
+
+
+def test_fp64_parity_workload1_full_grid(lib):
+    cr = synth.workload(1)
+    w, e, v = oracle_modes(cr)
+    ref, acc = oracle.rates4(cr, w, e, v)
+    out, st = run_gpu(lib, cr, w, e, v)
+    compare(out.reshape(1, -1), ref, RTOL_FP64)
+    assert np.array_equal(np.array(st["accepted"]), acc)
+    assert st["candidates"] == 3 * cr.nq ** 3 * cr.nb ** 4
+
+
+@pytest.mark.parametrize("tiles", [dict(block_j0=1, k1_tile=3, threads=64), dict(block_j0=3, k1_tile=7, threads=96),
+                                   dict(block_j0=3, k1_tile=64, threads=384)])
+def test_fp64_tilings_agree(lib, tiles):
+    cr = synth.simple_cubic((4, 3, 3))
+    w, e, v = oracle_modes(cr)
+    ref, acc = oracle.rates4(cr, w, e, v)
+    out, st = run_gpu(lib, cr, w, e, v, **tiles)
+    compare(out.reshape(1, -1), ref, RTOL_FP64)
+    assert np.array_equal(np.array(st["accepted"]), acc)
+
+
+def test_temperature_batch_and_dq_mode(lib):
+    cr = synth.licoo2((2, 2, 2))
+    w, e, v = oracle_modes(cr)
+    temps = [300.0, 500.0, 700.0]
+    for dq_mode in (0, 1):
+        ref, acc = oracle.rates4(cr, w, e, v, temps=temps, dq_mode=dq_mode)
+        out, st = run_gpu(lib, cr, w, e, v, temps=temps, dq_mode=dq_mode)
+        compare(out.reshape(3, -1), ref, RTOL_FP64)
+        assert np.array_equal(np.array(st["accepted"]), acc)
+
+
+def test_q_range_and_mask(lib):
+    cr = synth.diamond_si((3, 3, 2))
+    w, e, v = oracle_modes(cr)
+    nb = cr.nb
+    rng = np.random.Generator(np.random.PCG64(7))
+    mask = (rng.random(cr.nq * nb) < 0.3).astype(np.uint8)
+    sel = np.nonzero(mask)[0]
+    ref, _ = oracle.rates4(cr, w, e, v, sel=sel)
+    out, _ = run_gpu(lib, cr, w, e, v, mode_mask=mask)
+    flat = out.reshape(-1)
+    compare(flat[sel][None, :], ref, RTOL_FP64)
+    assert np.all(flat[mask == 0] == 0.0)
+    # q range [5, 11)
+    sel = np.arange(5 * nb, 11 * nb)
+    ref, _ = oracle.rates4(cr, w, e, v, sel=sel)
+    out, _ = run_gpu(lib, cr, w, e, v, q_begin=5, q_end=11)
+    flat = out.reshape(-1)
+    compare(flat[sel][None, :], ref, RTOL_FP64)
+    assert np.all(flat[:5 * nb] == 0.0) and np.all(flat[11 * nb:] == 0.0)
+
+
+def test_mixed_precision_bound(lib):
+    for cr in (synth.simple_cubic((4, 4, 4)), synth.diamond_si((3, 3, 3)), synth.licoo2((2, 2, 1))):
+        w, e, v = oracle_modes(cr)
+        ref, acc = oracle.rates4(cr, w, e, v)
+        out, st = run_gpu(lib, cr, w, e, v, precision=FP_PREC_MIXED)
+        err = compare(out.reshape(len(cr.temps), -1), ref, RTOL_MIXED)
+        assert np.array_equal(np.array(st["accepted"]), acc)
+        print(f"{cr.name} {cr.grid}: mixed max rel err {err:.3e}")
+
+
+def test_quadratic_scaling_bitwise(lib):
+    cr = synth.diamond_si((2, 2, 2))
+    w, e, v = oracle_modes(cr)
+    a, _ = run_gpu(lib, cr, w, e, v)
+    b, _ = run_gpu(lib, cr.scaled_fc4(2.0), w, e, v)
+    assert np.array_equal(b, 4.0 * a)
+    z, _ = run_gpu(lib, cr.scaled_fc4(0.0), w, e, v)
+    assert np.all(z == 0.0)
+
+
+def test_workload2_full_size_sampled_modes(lib):
+    """Diamond 8x8x8 (nb = 6), the benchmark's launch configuration, checked on sampled modes."""
+    cr = synth.workload(2)
+    w, e, v = oracle_modes(cr)
+    with lib.Context.from_crystal(cr) as ctx:
+        ctx.set_modes(w, e, v)
+        out, st = ctx.rates4(cr.temps, cr.scalebroad)
+    rng = np.random.Generator(np.random.PCG64(2104))
+    sel = np.sort(rng.choice(np.arange(cr.nb, cr.nq * cr.nb), size=3, replace=False))
+    ref, _ = oracle.rates4(cr, w, e, v, sel=sel)
+    compare(out.reshape(1, -1)[:, sel], ref, RTOL_FP64)
