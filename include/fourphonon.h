@@ -129,6 +129,26 @@ int fp_rates4(fp_ctx* ctx, int nT, const double* T, double scalebroad, const fp_
 int fp_rates4_device(fp_ctx* ctx, int nT, const double* T, double scalebroad, const fp_rates_opts* opts,
                      double* d_rates, fp_stats* stats);
 
+/*
+ * fp_rates4_noalloc -- fp_rates4_device without any device allocation.  The paper has no counterpart;
+ * this is a service of the library for callers that must not call cudaMalloc/cudaFree during the call,
+ * e.g. an application whose device memory belongs to its own pool allocator with a fixed budget, or a
+ * latency-critical caller that cannot accept the device synchronisation cudaFree implies.
+ *
+ * Same arguments and results as fp_rates4_device (d_rates: device pointer, nT x N x nb doubles,
+ * caller-owned).  The context and its modes (fp_init, fp_modes or fp_set_modes) must already exist;
+ * this call only uses them.  All working memory (Bose weights, per-work-item partial sums, queue and
+ * accepted-term counters, temperatures, mode mask) comes from one static device array of 16 MiB that
+ * every GPU loading the library holds until the process exits.  The q'-tile is enlarged automatically
+ * to fit; a problem that still needs more than 16 MiB returns FP_EINVAL with the required size in
+ * fp_last_error() (use fp_rates4_device for it).  The first call on a device looks up the array's
+ * device address on that device; make that first call before starting any stream capture.  Every call
+ * shares the array (counters are cleared on each call), so calls whose GPU work overlaps -- other
+ * streams, other contexts on the same device, other host threads -- race and must be serialised.
+ */
+int fp_rates4_noalloc(fp_ctx* ctx, int nT, const double* T, double scalebroad, const fp_rates_opts* opts,
+                      double* d_rates, fp_stats* stats);
+
 /* Release the context and all its device memory.  NULL is ignored. */
 void fp_free(fp_ctx* ctx);
 
