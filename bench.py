@@ -29,6 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2104_04895_gb300 import synth  # noqa: E402
+from paper_2104_04895_gb300.sharding import max_over_ranks, shard  # noqa: E402
 
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (recipe nominal; 152 SMs x 2070 MHz x 2 DFMA/clk/SM x 2 = 1.26)
 FP32_PEAK_TFLOPS = 80.5   # 152 SMs x 2070 MHz x 128 FFMA/clk/SM x 2
@@ -45,6 +46,8 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--cpu-sample-seconds", type=float, default=15.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--grid", type=int, nargs=3, default=None,
+                   help="override the workload's q-grid (small profiling cases only; not a bench line)")
     return p.parse_args()
 
 
@@ -53,10 +56,6 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
-
-
-def shard(N, ws, rank):
-    return (N * rank) // ws, (N * (rank + 1)) // ws
 
 
 class ClockSampler:
@@ -186,6 +185,8 @@ def main():
     dev = torch.device("cuda", local)
     prec = binding.FP_PREC_FP64 if args.precision == "fp64" else binding.FP_PREC_MIXED
     cr = synth.workload(args.workload)
+    if args.grid:
+        cr = cr.with_grid(args.grid)
     N, nb, nT = cr.nq, cr.nb, len(cr.temps)
     q0, q1 = shard(N, ws, rank)
 
@@ -221,10 +222,7 @@ def main():
     barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = float(sum(step_ms))
-    if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist if ws > 1 else None, dev)
     cands_step = 3.0 * N * N * N * nb ** 4          # all ranks together: one full-grid rate set per step
     value = cands_step * args.steps / (total_ms * 1e-3)
     flops_launch = st["flops"]
@@ -235,7 +233,7 @@ def main():
     # end to end through the public API with host buffers
     e2e_times = []
     h2d = d2h = 0
-    for i in range(args.e2e_steps + 1):
+    for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
@@ -247,11 +245,8 @@ def main():
             e2e_times.append(t1 - t0)
         h2d = 8 * (9 + cr.natoms * 4 + len(cr.temps)) + 96 * len(cr.fc2_idx) + 704 * len(cr.fc4_idx)
         d2h = r.nbytes
-    e2e_s = float(np.mean(e2e_times))
-    if ws > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = float(np.mean(e2e_times)) if e2e_times else float("nan")
+    e2e_s = max_over_ranks(e2e_s, dist if ws > 1 else None, dev)
     e2e_value = cands_step / e2e_s
 
     line = None
@@ -270,7 +265,9 @@ def main():
             "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
             "dtype": "f64" if prec == binding.FP_PREC_FP64 else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": synth.WORKLOAD_NAMES[args.workload], "precision": args.precision,
+            "config": {"workload": synth.WORKLOAD_NAMES[args.workload] if not args.grid else
+                   f"{cr.name} {args.grid[0]}x{args.grid[1]}x{args.grid[2]} (profiling case)",
+                   "precision": args.precision,
                        "candidates_per_step": cands_step, "accepted_per_step": st["accepted"],
                        "l2": "flushed between timed steps (256 MB write)", "tile": st["tile"],
                        "parallelism": f"q-partition over {ws} GPU(s)"},

@@ -51,6 +51,9 @@ def lib():
         L.oracle_v4.restype = ctypes.c_int
         L.oracle_v4.argtypes = [ip, dp, ctypes.c_int, dp, ctypes.c_int, ip, dp, dp, ctypes.c_int,
                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, ip]
+        L.oracle_phase3.restype = ctypes.c_int
+        L.oracle_phase3.argtypes = [ip, dp, ctypes.c_int, dp, dp, ctypes.c_int, dp, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int, ip, dp, dp]
         L.oracle_bose.restype = ctypes.c_double
         L.oracle_bose.argtypes = [ctypes.c_double, ctypes.c_double]
         L.oracle_prefactor.restype = ctypes.c_double
@@ -122,6 +125,29 @@ def v4(cryst, evec, q, q1, q2, process):
     if rc != 0:
         raise ValueError("oracle_v4 rejected its arguments")
     return out[..., 0] + 1j * out[..., 1], q3.value
+
+
+def phase3(cryst, omega, vel, temps=None, scalebroad=None, window=2.0, sigma_min=1e-10, dq_mode=0, sel=None):
+    """Three-phonon-like phase space P3 (nsel,) and weighted WP3 (nT, nsel) of modes sel (default all)."""
+    temps = cryst.temps if temps is None else temps
+    sb = cryst.scalebroad if scalebroad is None else scalebroad
+    if sel is None:
+        sel = np.arange(cryst.nq * cryst.nb)
+    sel_a, sel_p = _i(np.asarray(sel))
+    grid, grid_p = _i(np.asarray(cryst.grid))
+    lat, lat_p = _d(cryst.lattice)
+    om, om_p = _d(omega)
+    ve, ve_p = _d(vel)
+    T, T_p = _d(np.asarray(temps, float))
+    p3 = np.zeros(len(sel_a))
+    wp3 = np.zeros((len(T), len(sel_a)))
+    rc = lib().oracle_phase3(grid_p, lat_p, cryst.natoms, om_p, ve_p, len(T), T_p, float(sb), float(window),
+                             float(sigma_min), int(dq_mode), len(sel_a), sel_p,
+                             p3.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                             wp3.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if rc != 0:
+        raise ValueError("oracle_phase3 rejected its arguments")
+    return p3, wp3
 
 
 def bose(w, T):

@@ -367,3 +367,67 @@ double oracle_prefactor(int nq) {
   const double c = orc_conv();
   return M_PI * ORC_HBAR * ORC_HBAR * c * c * c * c / (8.0 * (double)nq * (double)nq);
 }
+
+/*
+ * Three-phonon-like phase space of selected modes (features of the surrogate; the paper's P3 / WP3
+ * outputs, Sec. 2.1, with the weighting of Eq. 3phgamma without |V3|^2 and without hbar pi / 4):
+ *   (+): q'' = q + q', dw = (w + w') - w'';  (-): q'' = q - q', dw = (w - w') - w''
+ *   sigma = sb |v(q',j') - v(q'',j'')| |dq|, the same window and Gaussian as the four-phonon rates.
+ *   p3[s]        = (1/N) sum [ delta+ + 1/2 delta- ]
+ *   wp3[t*nsel+s] = (1/N) sum [ (n' - n'') delta+ + 1/2 (n' + n'' + 1) delta- ] / (w w' w'')
+ */
+int oracle_phase3(const int grid[3], const double lattice[9], int natoms, const double* omega, const double* vel,
+                  int nT, const double* T, double scalebroad, double window, double sigma_min, int dq_mode,
+                  int nsel, const int* sel, double* p3, double* wp3) {
+  if (!grid || !lattice || natoms <= 0 || nT <= 0 || nsel < 0) return -1;
+  orc_problem P;
+  orc_setup(&P, grid, lattice, natoms, NULL, 0, NULL, NULL, omega, NULL, vel);
+  const int nb = P.nb, nq = P.nq;
+  const double dq = orc_dq_iso(&P);
+  memset(p3, 0, sizeof(double) * (size_t)nsel);
+  memset(wp3, 0, sizeof(double) * (size_t)nsel * nT);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int s = 0; s < nsel; ++s) {
+    const int q = sel[s] / nb;
+    const double w = omega[sel[s]];
+    if (w == 0.0) continue;
+    double acc_p = 0.0;
+    double acc_w[64];
+    for (int it = 0; it < nT && it < 64; ++it) acc_w[it] = 0.0;
+    for (int q1 = 0; q1 < nq; ++q1) {
+      for (int pm = 0; pm < 2; ++pm) {
+        const int sgn = pm == 0 ? +1 : -1;
+        int g[3], g1[3], g2[3];
+        orc_unidx(&P, q, g);
+        orc_unidx(&P, q1, g1);
+        for (int a = 0; a < 3; ++a) g2[a] = orc_wrap(g[a] + sgn * g1[a], P.grid[a]);
+        const int q2 = orc_idx(&P, g2);
+        for (int j1 = 0; j1 < nb; ++j1) {
+          const double w1 = omega[q1 * nb + j1];
+          if (w1 == 0.0) continue;
+          for (int j2 = 0; j2 < nb; ++j2) {
+            const double w2 = omega[q2 * nb + j2];
+            if (w2 == 0.0) continue;
+            const double t = (sgn > 0) ? (w + w1) : (w - w1);
+            const double dw = t - w2;
+            const double sigma = orc_sigma(&P, vel + 3 * (q1 * nb + j1), vel + 3 * (q2 * nb + j2), scalebroad, dq,
+                                           dq_mode);
+            const double sw = (sigma < sigma_min) ? sigma_min : sigma;
+            if (!(fabs(dw) <= window * sw)) continue;
+            const double delta =
+                (sigma < sigma_min) ? 1.0 : exp(-(dw * dw) / (sigma * sigma)) / (sqrt(M_PI) * sigma);
+            acc_p += (sgn > 0 ? 1.0 : 0.5) * delta;
+            for (int it = 0; it < nT && it < 64; ++it) {
+              const double n1 = orc_bose(w1, T[it]), n2 = orc_bose(w2, T[it]);
+              const double B = (sgn > 0) ? (n1 - n2) : 0.5 * (n1 + n2 + 1.0);
+              acc_w[it] += B * delta / (w * w1 * w2);
+            }
+          }
+        }
+      }
+    }
+    p3[s] = acc_p / (double)nq;
+    for (int it = 0; it < nT && it < 64; ++it) wp3[(size_t)it * nsel + s] = acc_w[it] / (double)nq;
+  }
+  return 0;
+}

@@ -15,9 +15,18 @@
 //   W[j0][j1][j2][j3]       = sum_{(k g)} T[..][(k g)][j3] e_{kg}(k2,j2)
 // Groups collect quartets with equal (atom k, atom l, D = R_k - R_l).
 //
-// Window and Gaussian (Sec. 2.4): dw = ((w0 +- w') +- w'') - w''' in FP64 without contraction,
-// sigma = (sb * sqrt((dx^2 + dy^2) + dz^2)) * dq, accept iff |dw| <= window * max(sigma, sigma_min),
-// delta = exp(-(dw/sigma)^2)/(sqrt(pi) sigma), or 1 when sigma < sigma_min.
+// Window and Gaussian (Sec. 2.4): the decision |dw| <= window * max(sigma, sigma_min) is the FP64 one,
+// with dw = ((w0 +- w') +- w'') - w''' and sigma = (sb * sqrt((dx^2 + dy^2) + dz^2)) * dq evaluated in that
+// order without contraction.  An FP32 prefilter with a proven error margin settles almost every
+// candidate; only candidates inside the rounding band are re-evaluated in FP64, so decisions are
+// identical to the FP64 evaluation.  delta = exp(-(dw/sigma)^2)/(sqrt(pi) sigma), or 1 when
+// sigma < sigma_min.
+//
+// Precision of the two instantiations:
+//   double: vertex, sigma, dw, Gaussian, Bose weights and sums in FP64.
+//   float:  vertex assembly and contraction in FP32; dw from two-float frequencies (error-free sums,
+//           |error| <= 2^-44 sum(w)); sigma from two-float velocities; Gaussian and Bose weights in FP32;
+//           compensated (two-float) per-thread sums, FP64 across threads and work items.
 #include "fp_internal.cuh"
 
 namespace fp {
@@ -61,14 +70,32 @@ __device__ __forceinline__ int wrapi(int x, int n) {
   return r < 0 ? r + n : r;
 }
 
+// s + e = a + b exactly (Knuth's two-sum); the compiler does not reassociate FP additions.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// two-float split of a double: h + l = x to about 2^-48 |x|
+__device__ __forceinline__ void split2(double x, float& h, float& l) {
+  h = __double2float_rn(x);
+  l = __double2float_rn(x - (double)h);
+}
+
+constexpr float kRelS = 1.0f / 524288.0f;   // 2^-19: prefilter margin per unit of sum(w) and of sigma
+constexpr float kRelP = 1.0f / 4194304.0f;  // 2^-22: prefilter margin per unit of window*sigma
+constexpr float kAbsV = 1.0f / 1099511627776.0f;  // 2^-40: two-float velocity difference error per |v|_1
+
 // Shared-memory carve shared by the kernel and the host-side size query.
 struct Carve {
-  size_t E0, E1, E2, E3, Psi, A, T, Tw2, TwQ;  // complex element offsets
-  size_t ncx;                                  // complex elements total
-  size_t Om0, Om1, Om2, Om3, V1, V2, V3, Sig, W0, W1, W2, W3, Red;  // double offsets
-  size_t ndbl;
-  size_t Mask;  // byte offset after doubles
-  size_t bytes(size_t cx_size) const { return ncx * cx_size + ndbl * sizeof(double) + Mask + 16; }
+  size_t E0, E1, E2, E3, Psi, A, T, Tw2, TwQ, ncx;                       // complex elements
+  size_t Om0, Om1, Om2, Om3, V1, V2, V3, Sig, W0, W1, W2, W3, Red, ndbl;   // doubles
+  size_t Hq, Lq, H1, L1, H2, L2, H3, L3, VH1, VL1, VH2, VL2, VH3, VL3, Sigf, F0, F1, F2, F3, nflt;  // floats
+  size_t Mask;  // bytes
+  size_t bytes(size_t cx_size) const {
+    return ncx * cx_size + ndbl * sizeof(double) + nflt * sizeof(float) + Mask + 16;
+  }
 };
 
 __host__ __device__ inline Carve make_carve(int nb, int J, int G, int nquart, int nT, int threads) {
@@ -100,14 +127,35 @@ __host__ __device__ inline Carve make_carve(int nb, int J, int G, int nquart, in
   c.W3 = d; d += (size_t)nT * nb;
   c.Red = d; d += (size_t)(threads / 32) * nT;
   c.ndbl = d;
+  size_t f = 0;
+  c.Hq = f; f += J;
+  c.Lq = f; f += J;
+  c.H1 = f; f += nb;
+  c.L1 = f; f += nb;
+  c.H2 = f; f += nb;
+  c.L2 = f; f += nb;
+  c.H3 = f; f += nb;
+  c.L3 = f; f += nb;
+  c.VH1 = f; f += 3 * nb;
+  c.VL1 = f; f += 3 * nb;
+  c.VH2 = f; f += 3 * nb;
+  c.VL2 = f; f += 3 * nb;
+  c.VH3 = f; f += 3 * nb;
+  c.VL3 = f; f += 3 * nb;
+  c.Sigf = f; f += 12 * nb2;
+  c.F0 = f; f += (size_t)nT * J;
+  c.F1 = f; f += 2 * (size_t)nT * nb;
+  c.F2 = f; f += 2 * (size_t)nT * nb;
+  c.F3 = f; f += (size_t)nT * nb;
+  c.nflt = f;
   c.Mask = (size_t)J;
   return c;
 }
 
-// sigma table entry for the leg velocity vl (sign s = +1 or -1) and the outgoing mode velocity v3:
+// FP64 sigma entry for the leg velocity vl (sign s = +1 or -1) and the outgoing mode velocity v3:
 // out = (window * max(sigma, sigma_min), 1/sigma or -1 when delta := 1).
-__device__ __forceinline__ void sigma_entry(const RatesArgs& a, const double* vl, double s, const double* v3,
-                                            double* out) {
+__device__ __noinline__ void sigma_entry(const RatesArgs& a, const double* vl, double s, const double* v3,
+                                         double* out) {
   double dx = __dsub_rn(s * vl[0], v3[0]);
   double dy = __dsub_rn(s * vl[1], v3[1]);
   double dz = __dsub_rn(s * vl[2], v3[2]);
@@ -130,17 +178,66 @@ __device__ __forceinline__ void sigma_entry(const RatesArgs& a, const double* vl
   out[1] = small ? -1.0 : __drcp_rn(sigma);
 }
 
-// Gaussian delta of Sec. 2.4 for an accepted term
-__device__ __forceinline__ double gauss(double dw, double inv) {
-  if (inv < 0.0) return 1.0;
-  double x = dw * inv;
-  return exp(-x * x) * inv * kInvSqrtPi;
+// Prefilter entry from an exact FP64 entry: (P~, margin, 1/sigma~).
+__device__ __forceinline__ void sigma_f_from_exact(const double* ex, float* out) {
+  float P = __double2float_rn(ex[0]);
+  out[0] = P;
+  out[1] = kRelP * P;
+  out[2] = ex[1] < 0.0 ? -1.0f : __double2float_rn(ex[1]);
 }
+
+// FP32 sigma entry from two-float velocities (isotropic |dq| only), with a rigorous bound; entries whose
+// relation to sigma_min is not settled in FP32 fall back to the exact FP64 entry.
+__device__ __forceinline__ void sigma_entry_f32(const RatesArgs& a, const float* vlh, const float* vll, float s,
+                                                const float* v3h, const float* v3l, const double* vl64,
+                                                const double* v364, float* out) {
+  float d[3];
+  float v1n = 0.f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float h, e;
+    two_sum(s * vlh[c], -v3h[c], h, e);
+    d[c] = h + (e + (s * vll[c] - v3l[c]));
+    v1n += fabsf(vlh[c]) + fabsf(v3h[c]);
+  }
+  const float sbdq = (float)(a.sb * a.dq);
+  const float sig = sbdq * sqrtf(fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2])));
+  const float E = kRelS * sig + kAbsV * sbdq * v1n;
+  const float smin = (float)a.sigma_min;
+  const float window = (float)a.window;
+  if (sig - E > 2.0f * smin) {
+    const float P = window * sig;
+    out[0] = P;
+    out[1] = window * E + kRelP * P;
+    out[2] = 1.0f / sig;
+  } else if (sig + E < 0.5f * smin) {
+    const float P = __double2float_rn(a.window * a.sigma_min);
+    out[0] = P;
+    out[1] = kRelP * P;
+    out[2] = -1.0f;
+  } else {
+    double ex[2];
+    sigma_entry(a, vl64, (double)s, v364, ex);
+    sigma_f_from_exact(ex, out);
+  }
+}
+
+// exact FP64 energy mismatch of candidate c (order of the FP64 definition)
+__device__ __forceinline__ double dw_fp64(int c, double w0, double wx, double wy, double w3) {
+  const double first = c < 3 ? wx : wy, second = c < 3 ? wy : wx;
+  const double t1 = (c == 2 || c == 5) ? __dsub_rn(w0, first) : __dadd_rn(w0, first);
+  const double t2 = (c == 0 || c == 3) ? __dadd_rn(t1, second) : __dsub_rn(t1, second);
+  return __dsub_rn(t2, w3);
+}
+
+// candidate c: 0..2 = ordering A (partners (k1,x), (k2,y)) ++, +-, --; 3..5 = ordering B ((k2,y), (k1,x))
+__device__ __forceinline__ float mult_of(int c) { return (c % 3 == 2) ? (1.0f / 6.0f) : 0.5f; }
 
 template <typename R>
 __global__ void __launch_bounds__(384) rates_kernel(RatesArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long s_item;
+  constexpr bool kF64 = sizeof(R) == 8;
   const int nb = a.nb, J = a.J, G = a.G, nT = a.nT, N = a.N;
   const int nb2 = nb * nb, nb3 = nb2 * nb;
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -169,13 +266,34 @@ __global__ void __launch_bounds__(384) rates_kernel(RatesArgs a) {
   double* sW2 = db + cv.W2;
   double* sW3 = db + cv.W3;
   double* sRed = db + cv.Red;
-  unsigned char* sMask = reinterpret_cast<unsigned char*>(db + cv.ndbl);
+  float* fb = reinterpret_cast<float*>(db + cv.ndbl);
+  float* sHq = fb + cv.Hq;
+  float* sLq = fb + cv.Lq;
+  float* sH1 = fb + cv.H1;
+  float* sL1 = fb + cv.L1;
+  float* sH2 = fb + cv.H2;
+  float* sL2 = fb + cv.L2;
+  float* sH3 = fb + cv.H3;
+  float* sL3 = fb + cv.L3;
+  float* sVH1 = fb + cv.VH1;
+  float* sVL1 = fb + cv.VL1;
+  float* sVH2 = fb + cv.VH2;
+  float* sVL2 = fb + cv.VL2;
+  float* sVH3 = fb + cv.VH3;
+  float* sVL3 = fb + cv.VL3;
+  float* sSigf = fb + cv.Sigf;
+  float* sF0 = fb + cv.F0;
+  float* sF1 = fb + cv.F1;
+  float* sF2 = fb + cv.F2;
+  float* sF3 = fb + cv.F3;
+  unsigned char* sMask = reinterpret_cast<unsigned char*>(fb + cv.nflt);
 
   const int TPJ = nthr / J;  // threads per j0 in the accumulation phase (multiple of 32)
   const int my_jj = tid / TPJ;
   const int my_lane = tid % TPJ;
   unsigned long long cnt0 = 0, cnt1 = 0, cnt2 = 0;
   const size_t NM = (size_t)N * nb;
+  const bool f32_sigma = !kF64 && a.dq_mode == 0;
 
   for (;;) {
     if (tid == 0) s_item = (long long)atomicAdd(a.counter, 1ULL);
@@ -198,32 +316,50 @@ __global__ void __launch_bounds__(384) rates_kernel(RatesArgs a) {
       int m = q * nb + j0b + jj;
       double w = a.omega[m];
       sOm0[jj] = w;
+      split2(w, sHq[jj], sLq[jj]);
       sMask[jj] = (w > 0.0 && (a.mask == nullptr || a.mask[m])) ? 1 : 0;
     }
     for (int o = tid; o < nT * J; o += nthr) {
       int it = o / J, jj = o % J;
-      sW0[o] = a.wt[3 * ((size_t)it * NM + (size_t)q * nb + j0b + jj) + 0];
+      double w = a.wt[3 * ((size_t)it * NM + (size_t)q * nb + j0b + jj) + 0];
+      sW0[o] = w;
+      sF0[o] = (float)w;
     }
     __syncthreads();
     int any = 0;
     for (int jj = 0; jj < J; ++jj) any |= sMask[jj];
 
     double acc[kMaxT];
+    float acch[kMaxT], accl[kMaxT];
 #pragma unroll
-    for (int t = 0; t < kMaxT; ++t) acc[t] = 0.0;
+    for (int t = 0; t < kMaxT; ++t) {
+      acc[t] = 0.0;
+      acch[t] = 0.f;
+      accl[t] = 0.f;
+    }
 
     const int k1_begin = tile * a.t1;
     const int k1_end = min(N, k1_begin + a.t1);
     for (int k1 = any ? k1_begin : k1_end; k1 < k1_end; ++k1) {
       const int g1[3] = {k1 / (a.grid[1] * a.grid[2]), (k1 / a.grid[2]) % a.grid[1], k1 % a.grid[2]};
       for (int o = tid; o < nb2; o += nthr) sE1[o] = cload<R>(a.evec[(size_t)k1 * nb2 + o]);
-      for (int o = tid; o < nb; o += nthr) sOm1[o] = a.omega[k1 * nb + o];
-      for (int o = tid; o < 3 * nb; o += nthr) sV1[o] = a.vel[(size_t)k1 * nb * 3 + o];
+      for (int o = tid; o < nb; o += nthr) {
+        double w = a.omega[k1 * nb + o];
+        sOm1[o] = w;
+        split2(w, sH1[o], sL1[o]);
+      }
+      for (int o = tid; o < 3 * nb; o += nthr) {
+        double v = a.vel[(size_t)k1 * nb * 3 + o];
+        sV1[o] = v;
+        split2(v, sVH1[o], sVL1[o]);
+      }
       for (int o = tid; o < nT * nb; o += nthr) {
         int it = o / nb, j = o % nb;
         const double* w = a.wt + 3 * ((size_t)it * NM + (size_t)k1 * nb + j);
         sW1[2 * o] = w[1];
         sW1[2 * o + 1] = w[2];
+        sF1[2 * o] = (float)w[1];
+        sF1[2 * o + 1] = (float)w[2];
       }
       for (int Q = tid; Q < a.nquart; Q += nthr) {
         const int* m = a.qmeta + 9 * Q;
@@ -273,19 +409,29 @@ __global__ void __launch_bounds__(384) rates_kernel(RatesArgs a) {
           sE3[o] = cload<R>(a.evec[(size_t)k3 * nb2 + o]);
         }
         for (int o = tid; o < nb; o += nthr) {
-          sOm2[o] = a.omega[k2 * nb + o];
-          sOm3[o] = a.omega[k3 * nb + o];
+          double w2 = a.omega[k2 * nb + o], w3 = a.omega[k3 * nb + o];
+          sOm2[o] = w2;
+          sOm3[o] = w3;
+          split2(w2, sH2[o], sL2[o]);
+          split2(w3, sH3[o], sL3[o]);
         }
         for (int o = tid; o < 3 * nb; o += nthr) {
-          sV2[o] = a.vel[(size_t)k2 * nb * 3 + o];
-          sV3[o] = a.vel[(size_t)k3 * nb * 3 + o];
+          double v2 = a.vel[(size_t)k2 * nb * 3 + o], v3 = a.vel[(size_t)k3 * nb * 3 + o];
+          sV2[o] = v2;
+          sV3[o] = v3;
+          split2(v2, sVH2[o], sVL2[o]);
+          split2(v3, sVH3[o], sVL3[o]);
         }
         for (int o = tid; o < nT * nb; o += nthr) {
           int it = o / nb, j = o % nb;
           const double* w2 = a.wt + 3 * ((size_t)it * NM + (size_t)k2 * nb + j);
+          const double w3b = a.wt[3 * ((size_t)it * NM + (size_t)k3 * nb + j) + 2];
           sW2[2 * o] = w2[1];
           sW2[2 * o + 1] = w2[2];
-          sW3[o] = a.wt[3 * ((size_t)it * NM + (size_t)k3 * nb + j) + 2];
+          sW3[o] = w3b;
+          sF2[2 * o] = (float)w2[1];
+          sF2[2 * o + 1] = (float)w2[2];
+          sF3[o] = (float)w3b;
         }
         for (int gi = tid; gi < G; gi += nthr) {
           const int* gm = a.gmeta + 5 * gi;
@@ -294,11 +440,19 @@ __global__ void __launch_bounds__(384) rates_kernel(RatesArgs a) {
           sTw2[gi] = cload<R>(a.tw[(int)(e % a.L)]);
         }
         __syncthreads();
-        // sigma tables: [tab][u][j3], tab 0: v(k2,u)-v3, 1: -v(k2,u)-v3, 2: v(k1,u)-v3, 3: -v(k1,u)-v3
+        // sigma tables [tab][u][j3]: tab 0: v(k2,u)-v3, 1: -v(k2,u)-v3, 2: v(k1,u)-v3, 3: -v(k1,u)-v3
         for (int o = tid; o < 4 * nb2; o += nthr) {
           const int tab = o / nb2, u = (o / nb) % nb, j3 = o % nb;
           const double* vl = (tab < 2 ? sV2 : sV1) + 3 * u;
-          sigma_entry(a, vl, (tab & 1) ? -1.0 : 1.0, sV3 + 3 * j3, sSig + 2 * o);
+          const float sgn = (tab & 1) ? -1.0f : 1.0f;
+          if (f32_sigma) {
+            const float* vlh = (tab < 2 ? sVH2 : sVH1) + 3 * u;
+            const float* vll = (tab < 2 ? sVL2 : sVL1) + 3 * u;
+            sigma_entry_f32(a, vlh, vll, sgn, sVH3 + 3 * j3, sVL3 + 3 * j3, vl, sV3 + 3 * j3, sSigf + 3 * o);
+          } else {
+            sigma_entry(a, vl, (double)sgn, sV3 + 3 * j3, sSig + 2 * o);
+            sigma_f_from_exact(sSig + 2 * o, sSigf + 3 * o);
+          }
         }
         // assembly of A[jj][j1][c][d]
         for (int o = tid; o < J * nb3; o += nthr) {
@@ -334,61 +488,109 @@ __global__ void __launch_bounds__(384) rates_kernel(RatesArgs a) {
           sA[o] = sum;
         }
         __syncthreads();
-        // window, Gaussian, Bose weights; ordering A: partners (k1,x), (k2,y); ordering B: (k2,y), (k1,x)
+        // window, Gaussian, Bose weights
         if (my_jj < J && sMask[my_jj]) {
+          const float h0 = sHq[my_jj], l0 = sLq[my_jj];
           const double w0 = sOm0[my_jj];
-          const bool both = k1 != k2;
+          const int ncand = (k1 != k2) ? 6 : 3;
           for (int r = my_lane; r < nb3; r += TPJ) {
             const int x = r / nb2, y = (r / nb) % nb, j3 = r % nb;
-            const double wx = sOm1[x], wy = sOm2[y], w3 = sOm3[j3];
-            if (wx == 0.0 || wy == 0.0 || w3 == 0.0) continue;
+            const float hx = sH1[x], hy = sH2[y], h3 = sH3[j3];
+            if (hx == 0.f || hy == 0.f || h3 == 0.f) continue;
+            const float S = (h0 + hx) + (hy + h3);
+            const float ap = h0 + hx, am = h0 - hx, bp = h0 + hy, bm = h0 - hy;
+            const float dt[6] = {(ap + hy) - h3, (ap - hy) - h3, (am - hy) - h3,
+                                 (bp + hx) - h3, (bp - hx) - h3, (bm - hx) - h3};
+            unsigned accm = 0;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+              if (c >= ncand) break;
+              const int tab = (c < 3) ? (c == 0 ? 0 : 1) : (c == 3 ? 2 : 3);
+              const int ent = tab * nb2 + ((c < 3) ? y : x) * nb + j3;
+              const float P = sSigf[3 * ent], M = fmaf(kRelS, S, sSigf[3 * ent + 1]);
+              const float ad = fabsf(dt[c]);
+              if (ad > P + M) continue;
+              if (ad < P - M) {
+                accm |= 1u << c;
+                continue;
+              }
+              // rounding band: the FP64 decision
+              const double d64 = dw_fp64(c, w0, sOm1[x], sOm2[y], sOm3[j3]);
+              double P64;
+              if (kF64 || !f32_sigma) {
+                P64 = sSig[2 * ent];
+              } else {
+                double ex[2];
+                const double* vl = ((tab < 2) ? sV2 + 3 * y : sV1 + 3 * x);
+                sigma_entry(a, vl, (tab & 1) ? -1.0 : 1.0, sV3 + 3 * j3, ex);
+                P64 = ex[0];
+              }
+              if (fabs(d64) <= P64) accm |= 1u << c;
+            }
+            if (!accm) continue;
             const Cx<R> Wv = sA[my_jj * nb3 + r];
-            const double W2 = (double)Wv.re * (double)Wv.re + (double)Wv.im * (double)Wv.im;
-            const double* sA0 = sSig + 2 * (0 * nb2 + y * nb + j3);
-            const double* sA1 = sSig + 2 * (1 * nb2 + y * nb + j3);
-            const double* sB0 = sSig + 2 * (2 * nb2 + x * nb + j3);
-            const double* sB1 = sSig + 2 * (3 * nb2 + x * nb + j3);
-            double f[6];
-            int pid[6];
-            int nacc = 0;
-            {
-              double d = __dsub_rn(__dadd_rn(__dadd_rn(w0, wx), wy), w3);
-              if (fabs(d) <= sA0[0]) { f[nacc] = 0.5 * gauss(d, sA0[1]); pid[nacc++] = 0; }
-              d = __dsub_rn(__dsub_rn(__dadd_rn(w0, wx), wy), w3);
-              if (fabs(d) <= sA1[0]) { f[nacc] = 0.5 * gauss(d, sA1[1]); pid[nacc++] = 1; }
-              d = __dsub_rn(__dsub_rn(__dsub_rn(w0, wx), wy), w3);
-              if (fabs(d) <= sA1[0]) { f[nacc] = (1.0 / 6.0) * gauss(d, sA1[1]); pid[nacc++] = 2; }
-            }
-            if (both) {
-              double d = __dsub_rn(__dadd_rn(__dadd_rn(w0, wy), wx), w3);
-              if (fabs(d) <= sB0[0]) { f[nacc] = 0.5 * gauss(d, sB0[1]); pid[nacc++] = 3; }
-              d = __dsub_rn(__dsub_rn(__dadd_rn(w0, wy), wx), w3);
-              if (fabs(d) <= sB1[0]) { f[nacc] = 0.5 * gauss(d, sB1[1]); pid[nacc++] = 4; }
-              d = __dsub_rn(__dsub_rn(__dsub_rn(w0, wy), wx), w3);
-              if (fabs(d) <= sB1[0]) { f[nacc] = (1.0 / 6.0) * gauss(d, sB1[1]); pid[nacc++] = 5; }
-            }
-            for (int k = 0; k < nacc; ++k) {
-              const int p = pid[k] % 3;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+              if (!(accm & (1u << c))) continue;
+              const int p = c % 3;
               cnt0 += (p == 0);
               cnt1 += (p == 1);
               cnt2 += (p == 2);
-              const bool ordA = pid[k] < 3;
-              const double base = f[k] * W2;
-#pragma unroll
-              for (int t = 0; t < kMaxT; ++t) {
-                if (t >= nT) break;
-                const double* w1t = sW1 + 2 * (t * nb);
-                const double* w2t = sW2 + 2 * (t * nb);
-                // (1+n)/w and n/w of the partner legs; k3 leg always n/w
-                double f1, f2;
-                if (ordA) {
-                  f1 = (p == 2) ? w1t[2 * x + 1] : w1t[2 * x];      // leg q' = k1
-                  f2 = (p == 0) ? w2t[2 * y] : w2t[2 * y + 1];      // leg q'' = k2
-                } else {
-                  f1 = (p == 2) ? w2t[2 * y + 1] : w2t[2 * y];      // leg q' = k2
-                  f2 = (p == 0) ? w1t[2 * x] : w1t[2 * x + 1];      // leg q'' = k1
+              const bool ordA = c < 3;
+              const int tab = (c < 3) ? (c == 0 ? 0 : 1) : (c == 3 ? 2 : 3);
+              const int ent = tab * nb2 + (ordA ? y : x) * nb + j3;
+              // Bose factor selectors: leg q' gets (1+n)/w unless --, leg q'' gets (1+n)/w only for ++
+              const int s1 = (p == 2) ? 1 : 0, s2 = (p == 0) ? 0 : 1;
+              const int i1 = ordA ? x : y, i2 = ordA ? y : x;
+              if constexpr (kF64) {
+                const double W2 = Wv.re * Wv.re + Wv.im * Wv.im;
+                const double d64 = dw_fp64(c, w0, sOm1[x], sOm2[y], sOm3[j3]);
+                const double inv = sSig[2 * ent + 1];
+                double delta = 1.0;
+                if (inv >= 0.0) {
+                  const double xx = d64 * inv;
+                  delta = exp(-xx * xx) * inv * kInvSqrtPi;
                 }
-                acc[t] += base * sW0[t * J + my_jj] * f1 * f2 * sW3[t * nb + j3];
+                const double base = (p == 2 ? (1.0 / 6.0) : 0.5) * W2 * delta;
+                const double* wq1 = ordA ? sW1 : sW2;  // table of leg q'
+                const double* wq2 = ordA ? sW2 : sW1;  // table of leg q''
+#pragma unroll
+                for (int t = 0; t < kMaxT; ++t) {
+                  if (t >= nT) break;
+                  acc[t] += base * sW0[t * J + my_jj] * wq1[2 * (t * nb + i1) + s1] * wq2[2 * (t * nb + i2) + s2] *
+                            sW3[t * nb + j3];
+                }
+              } else {
+                const float W2 = Wv.re * Wv.re + Wv.im * Wv.im;
+                // dw from two-float frequencies with error-free sums
+                const float fh = ordA ? hx : hy, fl = ordA ? sL1[x] : sL2[y];
+                const float sh = ordA ? hy : hx, sl = ordA ? sL2[y] : sL1[x];
+                const float sg1 = (p == 2) ? -1.f : 1.f, sg2 = (p == 0) ? 1.f : -1.f;
+                float t0, e1, e2, e3;
+                two_sum(h0, sg1 * fh, t0, e1);
+                two_sum(t0, sg2 * sh, t0, e2);
+                two_sum(t0, -h3, t0, e3);
+                const float lo = (((l0 + sg1 * fl) + sg2 * sl) - sL3[j3]) + ((e1 + e2) + e3);
+                const float dwf = t0 + lo;
+                const float inv = sSigf[3 * ent + 2];
+                float delta = 1.0f;
+                if (inv >= 0.f) {
+                  const float xx = dwf * inv;
+                  delta = __expf(-xx * xx) * inv * (float)kInvSqrtPi;
+                }
+                const float base = mult_of(c) * W2 * delta;
+                const float* fq1 = ordA ? sF1 : sF2;
+                const float* fq2 = ordA ? sF2 : sF1;
+#pragma unroll
+                for (int t = 0; t < kMaxT; ++t) {
+                  if (t >= nT) break;
+                  const float term = base * sF0[t * J + my_jj] * fq1[2 * (t * nb + i1) + s1] *
+                                     fq2[2 * (t * nb + i2) + s2] * sF3[t * nb + j3];
+                  float s, e;
+                  two_sum(acch[t], term, s, e);
+                  acch[t] = s;
+                  accl[t] += e;
+                }
               }
             }
           }
@@ -401,7 +603,7 @@ __global__ void __launch_bounds__(384) rates_kernel(RatesArgs a) {
 #pragma unroll
     for (int t = 0; t < kMaxT; ++t) {
       if (t >= nT) break;
-      double v = acc[t];
+      double v = kF64 ? acc[t] : (double)acch[t] + (double)accl[t];
       for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
       if (lane == 0) sRed[warp * nT + t] = v;
     }
