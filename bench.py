@@ -46,6 +46,10 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--cpu-sample-seconds", type=float, default=15.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-other", action="store_true", help="skip timing the other precision")
+    p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--surrogate", action="store_true", help="learned-rate study instead of the bench line")
+    p.add_argument("--seed", type=int, default=2104)
     p.add_argument("--grid", type=int, nargs=3, default=None,
                    help="override the workload's q-grid (small profiling cases only; not a bench line)")
     return p.parse_args()
@@ -66,11 +70,13 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, device_index=0):
-        self.dev = device_index
+        self.dev = device_index  # -1: do not sample
         self.proc = None
         self.lines = []
 
     def __enter__(self):
+        if self.dev < 0:
+            return self
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -170,10 +176,37 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def time_precision(ctx, binding, torch, cr, prec, q0, q1, out, flush, stream, steps, warmup, barrier, clk=None):
+    """Time `steps` full rate sets (after `warmup`) with CUDA events on the library's stream."""
+    def step():
+        return ctx.rates4_device(cr.temps, out.data_ptr(), cr.scalebroad, precision=prec, q_begin=q0, q_end=q1)
+
+    for _ in range(warmup):
+        st = step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    kernel_ms = []
+    barrier()
+    torch.cuda.synchronize()
+    sampler = clk if clk is not None else ClockSampler(-1)
+    with sampler:
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            st = step()
+            ev[i][1].record(stream)
+            kernel_ms.append(st["ms"])
+        torch.cuda.synchronize()
+    barrier()
+    return float(sum(a.elapsed_time(b) for a, b in ev)), float(np.mean(kernel_ms)), st
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.surrogate:
+        return run_surrogate(args)
     import torch
     import torch.distributed as dist
     from paper_2104_04895_gb300 import binding
@@ -183,7 +216,8 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    prec = binding.FP_PREC_FP64 if args.precision == "fp64" else binding.FP_PREC_MIXED
+    main_prec = binding.FP_PREC_FP64 if args.precision == "fp64" else binding.FP_PREC_MIXED
+    other_prec = binding.FP_PREC_MIXED if main_prec == binding.FP_PREC_FP64 else binding.FP_PREC_FP64
     cr = synth.workload(args.workload)
     if args.grid:
         cr = cr.with_grid(args.grid)
@@ -199,36 +233,34 @@ def main():
     ctx.set_stream(stream.cuda_stream)
     w, e, v = ctx.modes()
     out = torch.zeros(nT * N * nb, dtype=torch.float64, device=dev)
+    out_other = torch.zeros(nT * N * nb, dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > 129 MB L2
+    tuned = None
+    if not args.no_autotune:
+        tuned, _ = ctx.autotune(cr.temps, cr.scalebroad, precision=binding.FP_PREC_MIXED)
 
-    def step():
-        return ctx.rates4_device(cr.temps, out.data_ptr(), cr.scalebroad, precision=prec, q_begin=q0, q_end=q1)
-
-    for _ in range(args.warmup):
-        st = step()
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    kernel_ms = []
-    barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            flush.zero_()
-            ev[i][0].record(stream)
-            st = step()
-            ev[i][1].record(stream)
-            kernel_ms.append(st["ms"])
-        torch.cuda.synchronize()
-    barrier()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(step_ms))
-    total_ms = max_over_ranks(total_ms, dist if ws > 1 else None, dev)
     cands_step = 3.0 * N * N * N * nb ** 4          # all ranks together: one full-grid rate set per step
+    clk = ClockSampler(local)
+    total_ms, kms, st = time_precision(ctx, binding, torch, cr, main_prec, q0, q1, out, flush, stream, args.steps,
+                                       args.warmup, barrier, clk)
+    total_ms = max_over_ranks(total_ms, dist if ws > 1 else None, dev)
     value = cands_step * args.steps / (total_ms * 1e-3)
-    flops_launch = st["flops"]
-    kms = float(np.mean(kernel_ms))
-    achieved_tflops = flops_launch / (kms * 1e-3) / 1e12
-    peak = FP64_PEAK_TFLOPS if prec == binding.FP_PREC_FP64 else FP32_PEAK_TFLOPS
+    achieved_tflops = st["flops"] / (kms * 1e-3) / 1e12
+    peak = FP64_PEAK_TFLOPS if main_prec == binding.FP_PREC_FP64 else FP32_PEAK_TFLOPS
+    other = None
+    if not args.no_other:
+        o_ms, o_kms, o_st = time_precision(ctx, binding, torch, cr, other_prec, q0, q1, out_other, flush, stream,
+                                           args.steps, args.warmup, barrier)
+        o_ms = max_over_ranks(o_ms, dist if ws > 1 else None, dev)
+        o_peak = FP64_PEAK_TFLOPS if other_prec == binding.FP_PREC_FP64 else FP32_PEAK_TFLOPS
+        o_ach = o_st["flops"] / (o_kms * 1e-3) / 1e12
+        other = {"precision": "fp64" if other_prec == binding.FP_PREC_FP64 else "mixed",
+                 "value": cands_step * args.steps / (o_ms * 1e-3), "unit": "process-terms/s",
+                 "s_per_rate_set": o_ms / args.steps * 1e-3, "tile": o_st["tile"],
+                 "roofline": {"bound": "alu", "achieved": o_ach, "peak": o_peak, "unit": "TFLOP/s",
+                              "frac": o_ach / o_peak,
+                              "pipe": "fp64" if other_prec == binding.FP_PREC_FP64 else "fp32",
+                              "kernel_ms": o_kms}}
 
     # end to end through the public API with host buffers
     e2e_times = []
@@ -239,7 +271,7 @@ def main():
         t0 = time.perf_counter()
         with binding.Context.from_crystal(cr, device=local) as c2:
             c2.modes(copy=False)
-            r, _ = c2.rates4(cr.temps, cr.scalebroad, precision=prec, q_begin=q0, q_end=q1)
+            r, _ = c2.rates4(cr.temps, cr.scalebroad, precision=main_prec, q_begin=q0, q_end=q1, **(tuned or {}))
         t1 = time.perf_counter()
         if i > 0:
             e2e_times.append(t1 - t0)
@@ -249,43 +281,81 @@ def main():
     e2e_s = max_over_ranks(e2e_s, dist if ws > 1 else None, dev)
     e2e_value = cands_step / e2e_s
 
-    line = None
     if rank == 0:
         base = None
-        rel_err = None
+        rel_err = rel_err_other = None
         if not args.no_cpu_baseline:
             base, sel, ref = cpu_baseline(cr, args.cpu_sample_seconds, w, e, v)
             gpu = out.view(nT, N * nb).cpu().numpy()[:, sel]
             rel_err = float(np.max(np.abs(gpu - ref) / np.abs(ref)))
+            if other is not None:
+                g2 = out_other.view(nT, N * nb).cpu().numpy()[:, sel]
+                other["rel_err_vs_oracle_sampled"] = float(np.max(np.abs(g2 - ref) / np.abs(ref)))
             base.pop("seconds", None)
         line = {
             "metric": "four-phonon process-terms/s", "value": value, "unit": "process-terms/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "s_per_rate_set": total_ms / args.steps * 1e-3,
             "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
-            "dtype": "f64" if prec == binding.FP_PREC_FP64 else "f32+f64",
+            "dtype": "f64" if main_prec == binding.FP_PREC_FP64 else "f32+f64",
             "data": "synthetic",
             "config": {"workload": synth.WORKLOAD_NAMES[args.workload] if not args.grid else
-                   f"{cr.name} {args.grid[0]}x{args.grid[1]}x{args.grid[2]} (profiling case)",
-                   "precision": args.precision,
+                       f"{cr.name} {args.grid[0]}x{args.grid[1]}x{args.grid[2]} (profiling case)",
+                       "precision": args.precision,
                        "candidates_per_step": cands_step, "accepted_per_step": st["accepted"],
                        "l2": "flushed between timed steps (256 MB write)", "tile": st["tile"],
+                       "autotuned_mixed_tile": tuned,
                        "parallelism": f"q-partition over {ws} GPU(s)"},
             "rel_err_vs_oracle_sampled": rel_err,
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved_tflops / peak, "traffic": None,
-                         "pipe": "fp64" if prec == binding.FP_PREC_FP64 else "fp32",
-                         "kernel_ms": kms, "flops_per_launch": flops_launch},
+                         "pipe": "fp64" if main_prec == binding.FP_PREC_FP64 else "fp32",
+                         "kernel_ms": kms, "flops_per_launch": st["flops"]},
+            "other_precision": other,
             "cpu_baseline": base,
             "e2e": {"value": e2e_value, "unit": "process-terms/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "s_per_rate_set": e2e_s},
-            "gpu_launches": 3 * args.steps,
+            "gpu_launches": 4 * args.steps,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
     ctx.close()
     if ws > 1:
         dist.destroy_process_group()
+
+
+def run_surrogate(args):
+    """Learned rates vs the temperature-batched exact mixed path on the same workload (one JSON line)."""
+    import torch
+    from paper_2104_04895_gb300 import binding
+    cr = synth.workload(args.workload)
+    if args.grid:
+        cr = cr.with_grid(args.grid)
+    with binding.Context.from_crystal(cr) as ctx:
+        ctx.modes(copy=False)
+        ctx.autotune(cr.temps, cr.scalebroad, precision=binding.FP_PREC_MIXED)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        exact, st = ctx.rates4(cr.temps, cr.scalebroad, precision=binding.FP_PREC_MIXED)
+        t_exact = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        rep = ctx.surrogate_fit(cr.temps, cr.scalebroad, seed=args.seed)
+        t_sur = time.perf_counter() - t0
+        rates, used = ctx.surrogate_rates()
+    pred = (used == 0) & (exact > 0)
+    rel = np.abs(rates[pred] - exact[pred]) / exact[pred]
+    pos = exact > 0
+    cands = 3.0 * cr.nq ** 3 * cr.nb ** 4
+    line = {"metric": "four-phonon rate set: surrogate vs exact", "workload": synth.WORKLOAD_NAMES.get(args.workload)
+            if not args.grid else f"{cr.name} {args.grid[0]}x{args.grid[1]}x{args.grid[2]} T={list(cr.temps)}",
+            "exact_mixed_s": t_exact, "exact_terms_per_s": cands / t_exact,
+            "surrogate_s": t_sur, "speedup": t_exact / t_sur,
+            "exact_share": float(used[pos].mean()), "predicted_entries": int(pred.sum()),
+            "predicted_rel_err": {"median": float(np.median(rel)) if rel.size else None,
+                                  "p90": float(np.quantile(rel, 0.9)) if rel.size else None,
+                                  "max": float(rel.max()) if rel.size else None},
+            "report": rep}
+    print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

@@ -68,7 +68,9 @@ typedef struct {
   int q_begin, q_end;              /* q-points [q_begin, q_end) get rates (others 0); q_end <= 0 means N */
   int block_j0;                    /* kernel tile: branches j per work item (must divide nb); 0 = auto */
   int k1_tile;                     /* kernel tile: q' points per work item; 0 = auto */
-  int threads;                     /* threads per block; 0 = auto */
+  int threads;                     /* threads per block (>= block_j0 * nb^2, multiple of 32); 0 = auto */
+  int no_graph;                    /* 0: run the device part as a CUDA graph, captured on first use and replayed
+                                      while the launch parameters are unchanged; 1: plain stream launches */
 } fp_rates_opts;
 
 /* Counters of one fp_rates4 call. */
@@ -116,7 +118,7 @@ int fp_modes(fp_ctx* ctx, double* omega, double* evec, double* vel);
 int fp_set_modes(fp_ctx* ctx, const double* omega, const double* evec, const double* vel);
 
 /*
- * Four-phonon RTA rates (Eqs. tao0, 4phgamma, V4; Sec. 2.4) at nT temperatures T (K, > 0) with
+ * Four-phonon RTA rates (Eqs. tao0, 4phgamma, V4; Sec. 2.4) at nT <= 8 temperatures T (K, > 0) with
  * broadening scale `scalebroad` (> 0).  rates: host, nT x N x nb, ps^-1, written in full (modes not
  * selected by the mask / q-range, and zero-frequency modes, get 0).  opts and stats may be NULL.
  * Requires fp_modes or fp_set_modes first (FP_ESTATE otherwise).
@@ -128,6 +130,14 @@ int fp_rates4(fp_ctx* ctx, int nT, const double* T, double scalebroad, const fp_
  * the call returns after the work is complete on the context stream. */
 int fp_rates4_device(fp_ctx* ctx, int nT, const double* T, double scalebroad, const fp_rates_opts* opts,
                      double* d_rates, fp_stats* stats);
+
+/*
+ * Tile autotuner (the paper has no counterpart: it chooses launch tiles of this library's rate kernel).
+ * Times every admissible (block_j0, k1_tile, threads) on a sample of q-points with opts->precision and
+ * the given temperatures, writes the fastest into opts and remembers it in the context for calls whose
+ * tile fields are 0 at that precision and temperature count.  best_ms (nullable) receives its time.
+ */
+int fp_autotune(fp_ctx* ctx, int nT, const double* T, double scalebroad, fp_rates_opts* opts, double* best_ms);
 
 /*
  * fp_rates4_noalloc -- fp_rates4_device without any device allocation.  The paper has no counterpart;
@@ -148,6 +158,71 @@ int fp_rates4_device(fp_ctx* ctx, int nT, const double* T, double scalebroad, co
  */
 int fp_rates4_noalloc(fp_ctx* ctx, int nT, const double* T, double scalebroad, const fp_rates_opts* opts,
                       double* d_rates, fp_stats* stats);
+
+/* ---------------------------------------------------------------------------------------------------
+ * Phase space and the learned (surrogate) rates.
+ */
+
+/*
+ * Three-phonon-like phase space of every mode, used as features of the surrogate (the paper's P3 and
+ * WP3 outputs, Sec. 2.1, weighted as in Eq. 3phgamma without |V3|^2 and without hbar pi / 4):
+ * processes q'' = q + q' (dw = (w + w') - w'') and q'' = q - q' (dw = (w - w') - w''), with the window,
+ * Gaussian and small-sigma rule of fp_rates4 and sigma = scalebroad |v(q',j') - v(q'',j'')| |dq|.
+ *   p3[m]        = (1/N) sum [ delta+ + 1/2 delta- ]                                 (host, N x nb; ps)
+ *   wp3[t][m]    = (1/N) sum [ (n' - n'') delta+ + 1/2 (n' + n'' + 1) delta- ] / (w w' w'')   (host, nT x N x nb)
+ * Either output may be NULL.  Requires modes (FP_ESTATE otherwise).
+ */
+int fp_phase3(fp_ctx* ctx, int nT, const double* T, double scalebroad, const fp_rates_opts* opts, double* p3,
+              double* wp3);
+
+/* Number of parameters of the surrogate network for n_in input features (3 tanh layers of 128). */
+int fp_mlp_params_size(int n_in);
+
+/*
+ * Loss and gradient of the surrogate network on one batch, on `device`, with the library's FP32 kernels:
+ * y_hat = w4 . tanh(W3 tanh(W2 tanh(W1 x + b1) + b2) + b3) + b4, loss = mean (y_hat - y)^2.
+ * X: batch x n_in (row-major), y: batch, params/grad: fp_mlp_params_size(n_in) floats packed as
+ * W1 (128 x n_in), b1, W2 (128 x 128), b2, W3, b3, w4 (128), b4 (1).  Host pointers.
+ */
+int fp_mlp_loss_grad(int device, int n_in, int batch, const float* X, const float* y, const float* params,
+                     float* grad, float* loss);
+
+/* Options of fp_surrogate_fit; zero fields are not defaults: start from fp_surrogate_default_opts. */
+typedef struct {
+  double train_frac;       /* share of positive-frequency modes with exact training rates (0.10) */
+  double holdout_frac;     /* share of modes with exact rates that only judge the network (0.05) */
+  double tol;              /* mean held-out relative error above which a bin falls back to exact rates (0.05) */
+  unsigned long long seed; /* seeds the mode subsets, the initial weights and the minibatch order */
+  int epochs;              /* Adam epochs (400) */
+  int batch;               /* minibatch rows (1024) */
+  double lr;               /* Adam learning rate (2e-3) */
+  int precision;           /* precision of the exact evaluations, FP_PREC_* (mixed) */
+} fp_surrogate_opts;
+
+/* What fp_surrogate_fit did. */
+typedef struct {
+  int n_modes, n_train, n_holdout, n_fallback_modes, n_bins, n_bins_fallback;
+  double final_loss;
+  double holdout_median_rel_err, holdout_p90_rel_err, holdout_max_rel_err;
+  double ms_exact, ms_features, ms_train, ms_predict, ms_fallback, ms_total;
+} fp_surrogate_report;
+
+void fp_surrogate_default_opts(fp_surrogate_opts* opts);
+
+/*
+ * Learned four-phonon rates (the paper has no learned component).  Exact rates (fp_rates4) of a seeded
+ * train_frac share of the modes train a 3 x 128 tanh network on the GPU (hand-written forward, backward
+ * and Adam kernels) that maps per-mode features (w, |v|, branch, T, n0, P3, WP3, and the q-point as
+ * cos/sin(2 pi g_a / N_a)) to log(rate).  Exact
+ * rates of a further holdout_frac share judge it per bin (branch x frequency quartile); bins whose mean
+ * held-out relative error exceeds tol, and bins without held-out modes, are evaluated exactly.  Every
+ * trained, held-out or fallback mode keeps its exact rate.  Results are read with fp_surrogate_rates.
+ */
+int fp_surrogate_fit(fp_ctx* ctx, int nT, const double* T, double scalebroad, const fp_surrogate_opts* opts,
+                     fp_surrogate_report* report);
+
+/* Rates of the last fp_surrogate_fit (host, nT x N x nb) and per-entry flags: 1 = exact, 0 = predicted. */
+int fp_surrogate_rates(fp_ctx* ctx, double* rates, unsigned char* used_exact);
 
 /* Release the context and all its device memory.  NULL is ignored. */
 void fp_free(fp_ctx* ctx);

@@ -37,7 +37,7 @@ class fp_rates_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("window", ctypes.c_double), ("sigma_min", ctypes.c_double),
                 ("dq_mode", ctypes.c_int), ("mode_mask", ctypes.POINTER(ctypes.c_ubyte)),
                 ("q_begin", ctypes.c_int), ("q_end", ctypes.c_int), ("block_j0", ctypes.c_int),
-                ("k1_tile", ctypes.c_int), ("threads", ctypes.c_int)]
+                ("k1_tile", ctypes.c_int), ("threads", ctypes.c_int), ("no_graph", ctypes.c_int)]
 
 
 class fp_stats(ctypes.Structure):
@@ -50,7 +50,26 @@ class fp_stats(ctypes.Structure):
 
 
 EXPORTS = ["fp_version", "fp_default_opts", "fp_init", "fp_set_stream", "fp_modes", "fp_set_modes", "fp_rates4",
-           "fp_rates4_device", "fp_free", "fp_last_error"]
+           "fp_rates4_device", "fp_rates4_noalloc", "fp_autotune", "fp_phase3", "fp_mlp_params_size",
+           "fp_mlp_loss_grad", "fp_surrogate_default_opts", "fp_surrogate_fit", "fp_surrogate_rates", "fp_free",
+           "fp_last_error"]
+
+
+class fp_surrogate_opts(ctypes.Structure):
+    _fields_ = [("train_frac", ctypes.c_double), ("holdout_frac", ctypes.c_double), ("tol", ctypes.c_double),
+                ("seed", ctypes.c_ulonglong), ("epochs", ctypes.c_int), ("batch", ctypes.c_int),
+                ("lr", ctypes.c_double), ("precision", ctypes.c_int)]
+
+
+class fp_surrogate_report(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in ("n_modes", "n_train", "n_holdout", "n_fallback_modes", "n_bins",
+                                            "n_bins_fallback")] + \
+               [(n, ctypes.c_double) for n in ("final_loss", "holdout_median_rel_err", "holdout_p90_rel_err",
+                                               "holdout_max_rel_err", "ms_exact", "ms_features", "ms_train",
+                                               "ms_predict", "ms_fallback", "ms_total")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
 
 _LIB = None
 
@@ -94,6 +113,25 @@ def load(path: str | None = None):
     L.fp_rates4_device.argtypes = [vp, ctypes.c_int, dp, ctypes.c_double, ctypes.POINTER(fp_rates_opts), vp,
                                    ctypes.POINTER(fp_stats)]
     L.fp_rates4_device.restype = ctypes.c_int
+    L.fp_rates4_noalloc.argtypes = [vp, ctypes.c_int, dp, ctypes.c_double, ctypes.POINTER(fp_rates_opts), vp,
+                                    ctypes.POINTER(fp_stats)]
+    L.fp_rates4_noalloc.restype = ctypes.c_int
+    L.fp_autotune.argtypes = [vp, ctypes.c_int, dp, ctypes.c_double, ctypes.POINTER(fp_rates_opts), dp]
+    L.fp_autotune.restype = ctypes.c_int
+    L.fp_phase3.argtypes = [vp, ctypes.c_int, dp, ctypes.c_double, ctypes.POINTER(fp_rates_opts), dp, dp]
+    L.fp_phase3.restype = ctypes.c_int
+    L.fp_mlp_params_size.argtypes = [ctypes.c_int]
+    L.fp_mlp_params_size.restype = ctypes.c_int
+    fpp = ctypes.POINTER(ctypes.c_float)
+    L.fp_mlp_loss_grad.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, fpp, fpp, fpp, fpp, fpp]
+    L.fp_mlp_loss_grad.restype = ctypes.c_int
+    L.fp_surrogate_default_opts.argtypes = [ctypes.POINTER(fp_surrogate_opts)]
+    L.fp_surrogate_default_opts.restype = None
+    L.fp_surrogate_fit.argtypes = [vp, ctypes.c_int, dp, ctypes.c_double, ctypes.POINTER(fp_surrogate_opts),
+                                   ctypes.POINTER(fp_surrogate_report)]
+    L.fp_surrogate_fit.restype = ctypes.c_int
+    L.fp_surrogate_rates.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_ubyte)]
+    L.fp_surrogate_rates.restype = ctypes.c_int
     L.fp_free.argtypes = [vp]
     L.fp_free.restype = None
     L.fp_last_error.argtypes = [vp]
@@ -200,11 +238,12 @@ class Context:
 
     @staticmethod
     def make_opts(precision=FP_PREC_FP64, window=2.0, sigma_min=1e-10, dq_mode=0, mode_mask=None, q_begin=0,
-                  q_end=0, block_j0=0, k1_tile=0, threads=0):
+                  q_end=0, block_j0=0, k1_tile=0, threads=0, no_graph=0):
         o = fp_rates_opts()
         o.precision, o.window, o.sigma_min, o.dq_mode = int(precision), float(window), float(sigma_min), int(dq_mode)
         o.q_begin, o.q_end, o.block_j0, o.k1_tile, o.threads = int(q_begin), int(q_end), int(block_j0), \
             int(k1_tile), int(threads)
+        o.no_graph = int(no_graph)
         keep = None
         if mode_mask is not None:
             keep = np.ascontiguousarray(mode_mask, np.uint8)
@@ -230,3 +269,65 @@ class Context:
         _check(self.L, self.h, rc)
         del keep
         return st.as_dict()
+
+    def autotune(self, temps, scalebroad=1.0, **opts):
+        """Tile autotuning (fp_autotune); returns (tiles dict, best ms) and remembers the tiles in the context."""
+        T = np.ascontiguousarray(temps, np.float64).reshape(-1)
+        o, keep = self.make_opts(**opts)
+        best = ctypes.c_double(0.0)
+        _check(self.L, self.h, self.L.fp_autotune(self.h, len(T), _dp(T), float(scalebroad), ctypes.byref(o),
+                                                  ctypes.byref(best)))
+        del keep
+        return {"block_j0": o.block_j0, "k1_tile": o.k1_tile, "threads": o.threads}, best.value
+
+    def phase3(self, temps, scalebroad=1.0, **opts):
+        """Three-phonon-like phase space (fp_phase3): p3 (N*nb), wp3 (nT, N*nb)."""
+        T = np.ascontiguousarray(temps, np.float64).reshape(-1)
+        o, keep = self.make_opts(**opts)
+        p3 = np.zeros(self.N * self.nb)
+        wp3 = np.zeros((len(T), self.N * self.nb))
+        _check(self.L, self.h, self.L.fp_phase3(self.h, len(T), _dp(T), float(scalebroad), ctypes.byref(o),
+                                                _dp(p3), _dp(wp3)))
+        del keep
+        return p3, wp3
+
+    def surrogate_fit(self, temps, scalebroad=1.0, **sopts):
+        """Learned rates (fp_surrogate_fit); returns the report as a dict."""
+        T = np.ascontiguousarray(temps, np.float64).reshape(-1)
+        so = fp_surrogate_opts()
+        self.L.fp_surrogate_default_opts(ctypes.byref(so))
+        for k, v in sopts.items():
+            setattr(so, k, v)
+        rep = fp_surrogate_report()
+        _check(self.L, self.h, self.L.fp_surrogate_fit(self.h, len(T), _dp(T), float(scalebroad), ctypes.byref(so),
+                                                       ctypes.byref(rep)))
+        self._sur_nT = len(T)
+        return rep.as_dict()
+
+    def surrogate_rates(self):
+        """Rates of the last surrogate fit (nT, N, nb) and the exact-evaluation flags (same shape)."""
+        nT = self._sur_nT
+        r = np.zeros((nT, self.N, self.nb))
+        u = np.zeros((nT, self.N, self.nb), np.uint8)
+        _check(self.L, self.h, self.L.fp_surrogate_rates(self.h, _dp(r),
+                                                         u.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))))
+        return r, u
+
+
+def mlp_loss_grad(X, y, params, device=0):
+    """Loss and gradient of the surrogate network on one batch (fp_mlp_loss_grad, FP32 kernels)."""
+    L = load()
+    X = np.ascontiguousarray(X, np.float32)
+    y = np.ascontiguousarray(y, np.float32)
+    p = np.ascontiguousarray(params, np.float32)
+    B, F = X.shape
+    if L.fp_mlp_params_size(F) != p.size:
+        raise ValueError("parameter vector has the wrong size")
+    g = np.zeros_like(p)
+    loss = np.zeros(1, np.float32)
+    fpp = ctypes.POINTER(ctypes.c_float)
+    rc = L.fp_mlp_loss_grad(int(device), F, B, X.ctypes.data_as(fpp), y.ctypes.data_as(fpp), p.ctypes.data_as(fpp),
+                            g.ctypes.data_as(fpp), loss.ctypes.data_as(fpp))
+    if rc != FP_OK:
+        raise FourPhononError(rc, "fp_mlp_loss_grad failed")
+    return float(loss[0]), g

@@ -119,12 +119,9 @@ void fp_free(fp_ctx* c) {
   dfree(c->d_evec);
   dfree(c->d_vel);
   dfree(c->d_flag);
-  dfree(c->d_wt);
-  dfree(c->d_partial);
-  dfree(c->d_counters);
-  dfree(c->d_T);
-  dfree(c->d_mask);
+  dfree(c->d_scratch);
   dfree(c->d_rates);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -298,7 +295,6 @@ int fp_init(fp_ctx** out, const double lattice[9], int natoms, const double* fra
   INIT_CUDA(dalloc(&c->d_tw, (size_t)c->L));
   INIT_CUDA(fp::launch_twiddles(c, s));
   INIT_CUDA(dalloc(&c->d_flag, 1));
-  INIT_CUDA(dalloc(&c->d_counters, 4));
   INIT_CUDA(cudaStreamSynchronize(s));
   cudaFree(d_atoms4);
 #undef INIT_CUDA
@@ -368,168 +364,70 @@ int fp_set_modes(fp_ctx* c, const double* omega, const double* evec, const doubl
   return FP_OK;
 }
 
-static int rates_impl(fp_ctx* c, int nT, const double* T, double sb, const fp_rates_opts* user, double* d_out,
-                      fp_stats* stats) {
-  fp_rates_opts o;
-  fp_default_opts(&o);
+static int validate_opts(fp_ctx* c, int nT, const double* T, double sb, const fp_rates_opts* user,
+                         fp_rates_opts* o) {
+  fp_default_opts(o);
   if (user) {
-    o = *user;
-    if (o.window == 0.0) o.window = 2.0;
-    if (o.sigma_min == 0.0) o.sigma_min = 1e-10;
+    *o = *user;
+    if (o->window == 0.0) o->window = 2.0;
+    if (o->sigma_min == 0.0) o->sigma_min = 1e-10;
   }
   if (!c->have_modes) return fail(c, FP_ESTATE, "fp_rates4: call fp_modes or fp_set_modes first");
-  if (nT < 1 || nT > fp::kMaxT || !T) return fail(c, FP_EINVAL, "fp_rates4: nT must be in [1, 16]");
+  if (nT < 1 || nT > fp::kMaxT || !T) return fail(c, FP_EINVAL, "fp_rates4: nT must be in [1, 8]");
   for (int i = 0; i < nT; ++i)
     if (!(T[i] > 0.0) || !std::isfinite(T[i])) return fail(c, FP_EINVAL, "fp_rates4: temperatures must be > 0");
   if (!(sb > 0.0) || !std::isfinite(sb)) return fail(c, FP_EINVAL, "fp_rates4: scalebroad must be > 0");
-  if (!(o.window > 0.0) || !(o.sigma_min > 0.0)) return fail(c, FP_EINVAL, "fp_rates4: window, sigma_min > 0");
-  if (o.precision != FP_PREC_FP64 && o.precision != FP_PREC_MIXED)
+  if (!(o->window > 0.0) || !(o->sigma_min > 0.0)) return fail(c, FP_EINVAL, "fp_rates4: window, sigma_min > 0");
+  if (o->precision != FP_PREC_FP64 && o->precision != FP_PREC_MIXED)
     return fail(c, FP_EINVAL, "fp_rates4: unknown precision");
-  if (o.dq_mode != 0 && o.dq_mode != 1) return fail(c, FP_EINVAL, "fp_rates4: dq_mode must be 0 or 1");
-  const int N = c->N, nb = c->nb;
-  const int q_end = o.q_end <= 0 ? N : o.q_end;
-  if (o.q_begin < 0 || o.q_begin > q_end || q_end > N) return fail(c, FP_EINVAL, "fp_rates4: bad q range");
-  const int nq_sel = q_end - o.q_begin;
+  if (o->dq_mode != 0 && o->dq_mode != 1) return fail(c, FP_EINVAL, "fp_rates4: dq_mode must be 0 or 1");
+  return FP_OK;
+}
 
-  // tiles
-  int J = o.block_j0;
-  if (J <= 0) {
-    J = nb;
-    while (J > 1 && fp::rates_smem_bytes(o.precision, nb, J, c->G, c->nquart, nT, 384) > 112 * 1024) {
-      int nj = J - 1;
-      while (nj > 1 && nb % nj) --nj;
-      J = nj;
-    }
-  }
-  if (J < 1 || nb % J) return fail(c, FP_EINVAL, "fp_rates4: block_j0 must divide nb");
-  int threads = o.threads;
-  if (threads <= 0) {
-    threads = 32 * J;
-    while (threads < 160) threads += 32 * J;
-  }
-  if (threads % (32 * J) || threads > 384) return fail(c, FP_EINVAL, "fp_rates4: threads must be a multiple of 32*block_j0, <= 384");
-  int t1 = o.k1_tile > 0 ? o.k1_tile : (N + 511) / 512;
-  const int nchunk = nb / J;
-  const int ntile = (N + t1 - 1) / t1;
-  const long long n_items = (long long)ntile * nq_sel * nchunk;
-  const size_t smem = fp::rates_smem_bytes(o.precision, nb, J, c->G, c->nquart, nT, threads);
-  if (smem > 227 * 1024) return fail(c, FP_EINVAL, "fp_rates4: tile does not fit in shared memory");
-
+static int rates_impl(fp_ctx* c, int nT, const double* T, double sb, const fp_rates_opts* user, double* d_out,
+                      fp_stats* stats) {
+  fp_rates_opts o;
+  int rc = validate_opts(c, nT, T, sb, user, &o);
+  if (rc) return rc;
   FP_CUDA(c, cudaSetDevice(c->device));
-  cudaStream_t s = c->stream;
-  const size_t nm = (size_t)N * nb;
-  // scratch
-  size_t wt_need = 3 * nm * nT;
-  if (c->wt_cap < wt_need) {
-    dfree(c->d_wt);
-    c->wt_cap = 0;
-    FP_CUDA(c, dalloc(&c->d_wt, wt_need));
-    c->wt_cap = wt_need;
+  fp::Plan p;
+  std::string err;
+  rc = fp::plan_rates(c, o, nT, 0, &p, &err);
+  if (rc) return fail(c, rc, "fp_rates4: " + err);
+  size_t sz[13], total = 0;
+  fp::scratch_sizes(c, p, nT, o.mode_mask != nullptr, sz);
+  for (size_t x : sz) total += x;
+  if (c->scratch_cap < total) {
+    dfree(c->d_scratch);
+    c->scratch_cap = 0;
+    FP_CUDA(c, dalloc(&c->d_scratch, total));
+    c->scratch_cap = total;
   }
-  size_t part_need = (size_t)n_items * J * nT;
-  if (c->partial_cap < part_need) {
-    dfree(c->d_partial);
-    c->partial_cap = 0;
-    FP_CUDA(c, dalloc(&c->d_partial, part_need));
-    c->partial_cap = part_need;
+  unsigned char* b = c->d_scratch;
+  size_t off[13];
+  size_t acc = 0;
+  for (int i = 0; i < 13; ++i) {
+    off[i] = acc;
+    acc += sz[i];
   }
-  if (!c->d_T) FP_CUDA(c, dalloc(&c->d_T, (size_t)fp::kMaxT));
-  FP_CUDA(c, cudaMemcpyAsync(c->d_T, T, nT * sizeof(double), cudaMemcpyHostToDevice, s));
-  const unsigned char* d_mask = nullptr;
-  if (o.mode_mask) {
-    if (!c->d_mask) FP_CUDA(c, dalloc(&c->d_mask, nm));
-    FP_CUDA(c, cudaMemcpyAsync(c->d_mask, o.mode_mask, nm, cudaMemcpyHostToDevice, s));
-    d_mask = c->d_mask;
-  }
-  FP_CUDA(c, fp::launch_weights(c, nT, c->d_T, c->d_wt, s));
-
-  fp::RatesArgs a;
-  a.N = N;
-  a.nb = nb;
-  a.natoms = c->natoms;
-  a.nT = nT;
-  a.L = c->L;
-  a.G = c->G;
-  a.nquart = c->nquart;
-  for (int d = 0; d < 3; ++d) {
-    a.grid[d] = c->grid[d];
-    a.Lfac[d] = c->L / c->grid[d];
-  }
-  a.J = J;
-  a.t1 = t1;
-  a.nchunk = nchunk;
-  a.ntile = ntile;
-  a.q_begin = o.q_begin;
-  a.nq_sel = nq_sel;
-  a.n_items = n_items;
-  a.omega = c->d_omega;
-  a.evec = c->d_evec;
-  a.vel = c->d_vel;
-  a.wt = c->d_wt;
-  a.qmeta = c->d_qmeta;
-  a.qfc = c->d_qfc;
-  a.gmeta = c->d_gmeta;
-  a.grp_qstart = c->d_grp_qstart;
-  a.grp_q = c->d_grp_q;
-  a.kl_start = c->d_kl_start;
-  a.kl_grp = c->d_kl_grp;
-  a.tw = c->d_tw;
-  a.mask = d_mask;
-  a.sb = sb;
-  a.window = o.window;
-  a.sigma_min = o.sigma_min;
-  double B[9], detA;
-  reciprocal(c->lattice, B, &detA);
-  a.dq = std::cbrt(std::fabs(det3(B)) / (double)N);
-  a.dq_mode = o.dq_mode;
-  for (int i = 0; i < 9; ++i) a.rec[i] = B[i];
-  a.partial = c->d_partial;
-  a.counter = c->d_counters;
-  a.counts = c->d_counters + 1;
-
-  int per_sm = fp::rates_max_ctas_per_sm(o.precision, threads, smem);
-  if (per_sm < 1) return fail(c, FP_EINVAL, "fp_rates4: kernel tile cannot be resident on an SM");
-  int nsm = 0;
-  FP_CUDA(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
-  long long ctas = (long long)nsm * per_sm;
-  if (ctas > n_items) ctas = n_items > 0 ? n_items : 1;
-
-  FP_CUDA(c, cudaMemsetAsync(c->d_counters, 0, 4 * sizeof(unsigned long long), s));
-  FP_CUDA(c, cudaMemsetAsync(d_out, 0, (size_t)nT * nm * sizeof(double), s));
-  const double conv = fp::kConv;
-  const double pref = fp::kPi * fp::kHbar * fp::kHbar * conv * conv * conv * conv / (8.0 * (double)N * (double)N);
-  FP_CUDA(c, cudaEventRecord(c->ev0, s));
-  if (n_items > 0) {
-    FP_CUDA(c, fp::launch_rates(a, o.precision, threads, (int)ctas, smem, s));
-    FP_CUDA(c, fp::launch_reduce(a, pref, d_out, q_end, s));
-  }
-  FP_CUDA(c, cudaEventRecord(c->ev1, s));
+  fp::Scratch sc;
+  sc.counters = reinterpret_cast<unsigned long long*>(b + off[0]);
+  sc.T = reinterpret_cast<double*>(b + off[1]);
+  sc.mask = o.mode_mask ? b + off[2] : nullptr;
+  sc.wt = reinterpret_cast<double*>(b + off[3]);
+  sc.partial = reinterpret_cast<double*>(b + off[4]);
+  sc.omh = reinterpret_cast<float*>(b + off[5]);
+  sc.oml = reinterpret_cast<float*>(b + off[6]);
+  sc.velh = reinterpret_cast<float*>(b + off[7]);
+  sc.vell = reinterpret_cast<float*>(b + off[8]);
+  sc.evf = reinterpret_cast<float2*>(b + off[9]);
+  sc.qfcf = reinterpret_cast<float*>(b + off[10]);
+  sc.twf = reinterpret_cast<float2*>(b + off[11]);
+  sc.wtf = reinterpret_cast<float*>(b + off[12]);
   unsigned long long counts[4] = {0, 0, 0, 0};
-  FP_CUDA(c, cudaMemcpyAsync(counts, c->d_counters, sizeof(counts), cudaMemcpyDeviceToHost, s));
-  FP_CUDA(c, cudaStreamSynchronize(s));
-  if (stats) {
-    std::memset(stats, 0, sizeof(*stats));
-    double nsel = 0;
-    if (o.mode_mask) {
-      for (int q = o.q_begin; q < q_end; ++q)
-        for (int j = 0; j < nb; ++j) nsel += o.mode_mask[(size_t)q * nb + j] ? 1 : 0;
-    } else {
-      nsel = (double)nq_sel * nb;
-    }
-    stats->candidates = 3.0 * nsel * (double)N * (double)N * (double)nb * nb * nb;
-    for (int p = 0; p < 3; ++p) stats->accepted[p] = (double)counts[1 + p];
-    const double pairs = 0.5 * (double)N * (double)(N + 1);
-    const double per_pair = 8.0 * (9.0 * J * nb * c->G + 2.0 * J * (double)nb * nb * nb * nb);
-    const double prolog = 8.0 * 9.0 * J * nb * 9.0 * c->nquart;
-    stats->flops = (double)nq_sel * nchunk * (pairs * per_pair + (double)N * prolog);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-    stats->ms = ms;
-    stats->tile[0] = J;
-    stats->tile[1] = t1;
-    stats->tile[2] = threads;
-    stats->tile[3] = (int)ctas;
-  }
+  rc = fp::run_rates(c, o, p, sc, nT, T, sb, d_out, counts, o.no_graph == 0, &err);
+  if (rc) return fail(c, rc, "fp_rates4: " + err);
+  if (stats) fp::fill_stats(c, o, p, counts, stats);
   return FP_OK;
 }
 
@@ -544,7 +442,7 @@ int fp_rates4(fp_ctx* c, int nT, const double* T, double scalebroad, const fp_ra
               fp_stats* stats) {
   if (!c) return fail(nullptr, FP_EINVAL, "fp_rates4: NULL context");
   if (!rates) return fail(c, FP_EINVAL, "fp_rates4: NULL output");
-  if (nT < 1 || nT > fp::kMaxT) return fail(c, FP_EINVAL, "fp_rates4: nT must be in [1, 16]");
+  if (nT < 1 || nT > fp::kMaxT) return fail(c, FP_EINVAL, "fp_rates4: nT must be in [1, 8]");
   FP_CUDA(c, cudaSetDevice(c->device));
   const size_t need = (size_t)nT * c->N * c->nb;
   if (c->rates_cap < need) {

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <array>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -22,7 +23,7 @@ constexpr double kInvSqrtPi = 0.56418958354775628695;  // 1/sqrt(pi)
 constexpr double kPi = 3.14159265358979323846;
 
 constexpr int kMaxNb = 12;  // up to 4 atoms per cell (36 branches would not fit the on-chip tiles)
-constexpr int kMaxT = 16;   // temperatures per call
+constexpr int kMaxT = 8;    // temperatures per call
 
 // Work description of one rates launch (all device pointers).
 struct RatesArgs {
@@ -43,12 +44,45 @@ struct RatesArgs {
   const int* kl_grp;         // [G]
   const double2* tw;         // [L]: exp(2 pi i m / L)
   const unsigned char* mask; // [N*nb] or null
+  // FP32 copies prepared once per call (prep_kernel)
+  const float* omh;          // [N*nb] two-float frequencies: omh + oml = omega
+  const float* oml;
+  const float* velh;         // [N*nb*3] two-float velocities
+  const float* vell;
+  const float2* evf;         // [N][nb][nb]
+  const float* qfcf;         // [nquart][81]
+  const float2* twf;         // [L]
+  const float* wtf;          // [nT][N*nb][3]
   double sb, window, sigma_min, dq;
   int dq_mode;
   double rec[9];
   double* partial;           // [n_items][J][nT]
   unsigned long long* counter;
   unsigned long long* counts; // [3]
+};
+
+// Tile plan of one rates call.
+struct Plan {
+  int J, threads, t1, nchunk, ntile, nq_sel, q_begin, q_end, ctas;
+  long long n_items;
+  size_t smem;
+};
+
+// Device working memory of one rates call (owned by the caller of run_rates).
+struct Scratch {
+  unsigned long long* counters;  // [4]: queue, accepted ++, +-, --
+  double* T;                     // [kMaxT]
+  unsigned char* mask;           // [N*nb] or null
+  double* wt;                    // [nT][N*nb][3]
+  double* partial;               // [n_items][J][nT]
+  float* omh;                    // [N*nb]
+  float* oml;
+  float* velh;                   // [N*nb*3]
+  float* vell;
+  float2* evf;                   // [N*nb*nb]
+  float* qfcf;                   // [nquart*81]
+  float2* twf;                   // [L]
+  float* wtf;                    // [nT][N*nb][3]
 };
 
 }  // namespace fp
@@ -83,28 +117,42 @@ struct fp_ctx {
   double2* d_evec = nullptr;
   double* d_vel = nullptr;
   int* d_flag = nullptr;
-  // per-call scratch (grown on demand)
-  double* d_wt = nullptr;
-  size_t wt_cap = 0;
-  double* d_partial = nullptr;
-  size_t partial_cap = 0;
-  unsigned long long* d_counters = nullptr;  // [0]: queue, [1..3]: accepted counts
-  double* d_T = nullptr;
-  unsigned char* d_mask = nullptr;
+  // per-call working memory (grown on demand) and the output staging buffer of fp_rates4
+  unsigned char* d_scratch = nullptr;
+  size_t scratch_cap = 0;
   double* d_rates = nullptr;
   size_t rates_cap = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // tiles chosen by fp_autotune, per (precision, one or several temperatures): J, k1 tile, threads
+  int tuned[2][2][3] = {{{0, 0, 0}, {0, 0, 0}}, {{0, 0, 0}, {0, 0, 0}}};
+  // the captured rate step and the launch parameters it was captured with
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<unsigned char> graph_key;
+  // result of the last fp_surrogate_fit
+  int sur_nT = 0;
+  std::vector<double> sur_rates;
+  std::vector<unsigned char> sur_used;
   std::string err;
 };
 
 namespace fp {
-// Kernels launchers (implemented in fp_modes.cu / fp_rates.cu); each returns a cudaError_t.
+// Support kernels (fp_modes.cu).
 cudaError_t launch_scale_fc4(double* qfc, const int* d_atoms4, const double* d_mass, int nquart, cudaStream_t s);
 cudaError_t launch_twiddles(fp_ctx* c, cudaStream_t s);
 cudaError_t launch_modes(fp_ctx* c, cudaStream_t s);
 cudaError_t launch_weights(fp_ctx* c, int nT, const double* d_T, double* d_wt, cudaStream_t s);
-cudaError_t launch_rates(const RatesArgs& a, int precision, int threads, int ctas, size_t smem, cudaStream_t s);
-cudaError_t launch_reduce(const RatesArgs& a, double pref, double* d_rates, int q_end, cudaStream_t s);
-size_t rates_smem_bytes(int precision, int nb, int J, int G, int nquart, int nT, int threads);
-int rates_max_ctas_per_sm(int precision, int threads, size_t smem);
+
+// Rate path (fp_rates.cu).
+// Validate options and choose tiles; `partial_budget` (bytes, 0 = unlimited) enlarges the q'-tile until the
+// per-item partial sums fit.  Returns FP_OK or an FP_E* code with a message in *err.
+int plan_rates(fp_ctx* c, const fp_rates_opts& o, int nT, size_t partial_budget, Plan* p, std::string* err);
+// Byte sizes of the Scratch buffers of a plan (in the order of the Scratch fields).
+void scratch_sizes(const fp_ctx* c, const Plan& p, int nT, bool with_mask, size_t sizes[13]);
+// Enqueue weights, FP32 prep, the persistent rate kernel and the reduction on c->stream, then wait and
+// return the accepted counts.  d_out: nT x N x nb doubles (zeroed here).
+// use_graph: capture the device part once per set of launch parameters and replay it as a CUDA graph.
+int run_rates(fp_ctx* c, const fp_rates_opts& o, const Plan& p, const Scratch& s, int nT, const double* T,
+              double sb, double* d_out, unsigned long long counts[4], bool use_graph, std::string* err);
+void fill_stats(const fp_ctx* c, const fp_rates_opts& o, const Plan& p, const unsigned long long counts[4],
+                fp_stats* st);
 }  // namespace fp

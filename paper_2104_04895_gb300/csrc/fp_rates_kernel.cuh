@@ -1,0 +1,714 @@
+// Four-phonon RTA rate kernel template (paper Sec. 2.2 Eqs. tao0, 4phgamma, V4; Sec. 2.4).
+// Instantiated per precision in fp_rates_f64.cu and fp_rates_f32.cu; host logic is in fp_rates.cu.
+//
+// One function W serves all three processes.  With k3 = q + k1 + k2 (mod G) and e(-k) = conj e(k),
+//   W(q,j0; k1,j1; k2,j2; k3,j3) = sum_quartets sum_{abgt} Phi4/sqrt(M^4) e_a(q,j0) e_b(k1,j1) e_g(k2,j2)
+//                                  conj(e_t(k3,j3)) exp(i (k1.R_j + k2.R_k - k3.R_l))
+// gives V++(q,k1,k2) = W(q;k1,k2), V+-(q,k1,-k2) = W(q;k1,k2), V--(q,-k1,-k2) = W(q;k1,k2), and
+// W(q;k2,k1)[j0 j2 j1 j3] = W(q;k1,k2)[j0 j1 j2 j3] (transposition symmetry, Sec. 2.3 Eq. TS), so one W
+// per unordered pair {k1, k2} serves six (ordering, process) terms.
+//
+// The phase factorises as exp(i(k1.R_j - (q+k1).R_l)) * exp(i k2.(R_k - R_l)); the first factor and the
+// contractions with e(q) and e(k1) are hoisted out of the k2 loop:
+//   Psi[j0][j1][g][gt] = sum_{Q in group g} tw1_Q sum_{ab} phi_Q[a b g t] e_{ia}(q,j0) e_{jb}(k1,j1)
+//   A[j0][j1][(k g)][(l t)] = sum_{groups g of atoms (k,l)} exp(i k2.D_g) Psi[j0][j1][g][g t]
+//   T[j0][j1][(k g)][j3]    = sum_{(l t)} A[..][(l t)] conj(e_{lt}(k3,j3))
+//   W[j0][j1][j2][j3]       = sum_{(k g)} e_{kg}(k2,j2) T[..][(k g)][j3]
+// Groups collect quartets with equal (atom k, atom l, D = R_k - R_l).  Thread r < J*nb^2 owns the row
+// (j0, j1, c) when it builds A and T (registers -> shared T) and the row (j0, j1 = x, j2 = y) when it
+// builds W (registers) and screens the nb entries (x, y, j3) of that row, so W never leaves registers.
+//
+// Window and Gaussian (Sec. 2.4): the decision |dw| <= window * max(sigma, sigma_min) is the FP64 one,
+// with dw = ((w0 +- w') +- w'') - w''' and sigma = (sb * sqrt((dx^2 + dy^2) + dz^2)) * dq evaluated in that
+// order without contraction.  An FP32 prefilter with a proven error margin settles almost every
+// candidate; only candidates inside the rounding band are re-evaluated in FP64, so decisions are
+// identical to the FP64 evaluation.  delta = exp(-(dw/sigma)^2)/(sqrt(pi) sigma), or 1 when
+// sigma < sigma_min.
+//
+// Precision of the two instantiations:
+//   double: vertex, sigma, dw, Gaussian, Bose weights and sums in FP64.
+//   float:  vertex assembly and contraction in FP32; dw from two-float frequencies (error-free sums,
+//           |error| <= 2^-44 sum(w)); sigma from two-float velocities; Gaussian and Bose weights in FP32;
+//           compensated (two-float) per-thread sums, FP64 across threads and work items.
+#pragma once
+#include <cmath>
+#include <cstring>
+
+#include "fp_internal.cuh"
+
+namespace fp {
+namespace {
+
+template <typename R>
+struct __align__(2 * sizeof(R)) Cx {
+  R re, im;
+};
+
+template <typename R>
+__device__ __forceinline__ Cx<R> cmk(R a, R b) {
+  Cx<R> c;
+  c.re = a;
+  c.im = b;
+  return c;
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> cmul(Cx<R> a, Cx<R> b) {
+  return cmk<R>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+// acc += a * b
+template <typename R>
+__device__ __forceinline__ void cfma(Cx<R>& acc, Cx<R> a, Cx<R> b) {
+  acc.re = fma(a.re, b.re, fma(-a.im, b.im, acc.re));
+  acc.im = fma(a.re, b.im, fma(a.im, b.re, acc.im));
+}
+// acc += a * conj(b)
+template <typename R>
+__device__ __forceinline__ void cfma_conj(Cx<R>& acc, Cx<R> a, Cx<R> b) {
+  acc.re = fma(a.re, b.re, fma(a.im, b.im, acc.re));
+  acc.im = fma(a.im, b.re, fma(-a.re, b.im, acc.im));
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> ld_e(const RatesArgs& a, size_t i);
+template <>
+__device__ __forceinline__ Cx<double> ld_e<double>(const RatesArgs& a, size_t i) {
+  double2 d = a.evec[i];
+  return cmk<double>(d.x, d.y);
+}
+template <>
+__device__ __forceinline__ Cx<float> ld_e<float>(const RatesArgs& a, size_t i) {
+  float2 d = a.evf[i];
+  return cmk<float>(d.x, d.y);
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> ld_tw(const RatesArgs& a, int m);
+template <>
+__device__ __forceinline__ Cx<double> ld_tw<double>(const RatesArgs& a, int m) {
+  double2 d = a.tw[m];
+  return cmk<double>(d.x, d.y);
+}
+template <>
+__device__ __forceinline__ Cx<float> ld_tw<float>(const RatesArgs& a, int m) {
+  float2 d = a.twf[m];
+  return cmk<float>(d.x, d.y);
+}
+template <typename R>
+__device__ __forceinline__ R ld_fc(const RatesArgs& a, size_t i);
+template <>
+__device__ __forceinline__ double ld_fc<double>(const RatesArgs& a, size_t i) {
+  return a.qfc[i];
+}
+template <>
+__device__ __forceinline__ float ld_fc<float>(const RatesArgs& a, size_t i) {
+  return a.qfcf[i];
+}
+
+__device__ __forceinline__ int wrapi(int x, int n) {
+  int r = x % n;
+  return r < 0 ? r + n : r;
+}
+
+// s + e = a + b exactly (Knuth's two-sum); the compiler does not reassociate FP additions.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+constexpr float kRelS = 1.0f / 524288.0f;         // 2^-19: prefilter margin per unit of sum(w) and of sigma
+constexpr float kRelP = 1.0f / 4194304.0f;        // 2^-22: prefilter margin per unit of window*sigma
+constexpr float kAbsV = 1.0f / 1099511627776.0f;  // 2^-40: two-float velocity difference error per |v|_1
+
+// Shared-memory carve shared by the kernel and the host-side size query.
+struct Carve {
+  size_t E0, E1, E2, E3, Psi, T, Tw2, TwQ, ncx;                               // complex elements
+  size_t Om0, Om1, Om2, Om3, V1, V2, V3, Sig, W0, W1, W2, W3, Red, ndbl;       // doubles
+  size_t Hq, Lq, H1, L1, H2, L2, H3, L3, VH1, VL1, VH2, VL2, VH3, VL3, Sigf, F0, F1, F2, F3, nflt;  // floats
+  size_t KL, nint;                                                            // ints
+  size_t Mask;                                                                // bytes
+  size_t bytes(size_t cx_size) const {
+    return ncx * cx_size + ndbl * sizeof(double) + nflt * sizeof(float) + nint * sizeof(int) + Mask + 16;
+  }
+};
+
+__host__ __device__ inline Carve make_carve(int nb, int J, int G, int nquart, int nT, int threads) {
+  Carve c;
+  const size_t nb2 = (size_t)nb * nb, nb3 = nb2 * nb, na = nb / 3;
+  const size_t rows = (size_t)J * nb2;
+  size_t o = 0;
+  c.E0 = o; o += (size_t)J * nb;
+  c.E1 = o; o += nb2;
+  c.E2 = o; o += nb2;
+  c.E3 = o; o += nb2;
+  c.Psi = o; o += (size_t)J * nb * G * 9;
+  c.T = o; o += (size_t)J * nb * (nb2 + 1);  // (j0, j1) blocks padded by one entry (bank spread)
+  c.Tw2 = o; o += G;
+  c.TwQ = o; o += nquart;
+  c.ncx = o;
+  size_t d = 0;
+  c.Om0 = d; d += J;
+  c.Om1 = d; d += nb;
+  c.Om2 = d; d += nb;
+  c.Om3 = d; d += nb;
+  c.V1 = d; d += 3 * nb;
+  c.V2 = d; d += 3 * nb;
+  c.V3 = d; d += 3 * nb;
+  c.Sig = d; d += 8 * nb2;
+  c.W0 = d; d += (size_t)nT * J;
+  c.W1 = d; d += 2 * (size_t)nT * nb;
+  c.W2 = d; d += 2 * (size_t)nT * nb;
+  c.W3 = d; d += (size_t)nT * nb;
+  c.Red = d; d += rows * nT;
+  c.ndbl = d;
+  size_t f = 0;
+  c.Hq = f; f += J;
+  c.Lq = f; f += J;
+  c.H1 = f; f += nb;
+  c.L1 = f; f += nb;
+  c.H2 = f; f += nb;
+  c.L2 = f; f += nb;
+  c.H3 = f; f += nb;
+  c.L3 = f; f += nb;
+  c.VH1 = f; f += 3 * nb;
+  c.VL1 = f; f += 3 * nb;
+  c.VH2 = f; f += 3 * nb;
+  c.VL2 = f; f += 3 * nb;
+  c.VH3 = f; f += 3 * nb;
+  c.VL3 = f; f += 3 * nb;
+  c.Sigf = f; f += 12 * nb2;
+  c.F0 = f; f += (size_t)nT * J;
+  c.F1 = f; f += 2 * (size_t)nT * nb;
+  c.F2 = f; f += 2 * (size_t)nT * nb;
+  c.F3 = f; f += (size_t)nT * nb;
+  c.nflt = f;
+  size_t k = 0;
+  c.KL = k; k += na * na + 1 + G;
+  c.nint = k;
+  c.Mask = (size_t)J;
+  (void)threads;
+  return c;
+}
+
+// FP64 sigma entry for the leg velocity vl (sign s = +1 or -1) and the outgoing mode velocity v3:
+// out = (window * max(sigma, sigma_min), 1/sigma or -1 when delta := 1).
+__device__ __noinline__ void sigma_entry(const RatesArgs& a, const double* vl, double s, const double* v3,
+                                         double* out) {
+  double dx = __dsub_rn(s * vl[0], v3[0]);
+  double dy = __dsub_rn(s * vl[1], v3[1]);
+  double dz = __dsub_rn(s * vl[2], v3[2]);
+  double sigma;
+  if (a.dq_mode == 0) {
+    double s2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    sigma = __dmul_rn(__dmul_rn(a.sb, __dsqrt_rn(s2)), a.dq);
+  } else {
+    double p[3];
+    for (int ax = 0; ax < 3; ++ax) {
+      const double* b = a.rec + 3 * ax;
+      double t = __dadd_rn(__dadd_rn(__dmul_rn(dx, b[0]), __dmul_rn(dy, b[1])), __dmul_rn(dz, b[2]));
+      p[ax] = __ddiv_rn(t, (double)a.grid[ax]);
+    }
+    double s2 = __ddiv_rn(__dadd_rn(__dadd_rn(__dmul_rn(p[0], p[0]), __dmul_rn(p[1], p[1])), __dmul_rn(p[2], p[2])), 3.0);
+    sigma = __dmul_rn(a.sb, __dsqrt_rn(s2));
+  }
+  const bool small = sigma < a.sigma_min;
+  out[0] = __dmul_rn(a.window, small ? a.sigma_min : sigma);
+  out[1] = small ? -1.0 : __drcp_rn(sigma);
+}
+
+// Prefilter entry from an exact FP64 entry: (P~, margin) and 1/sigma~.
+__device__ __forceinline__ void sigma_f_from_exact(const double* ex, float2* pm, float* inv) {
+  float P = __double2float_rn(ex[0]);
+  *pm = make_float2(P, kRelP * P);
+  *inv = ex[1] < 0.0 ? -1.0f : __double2float_rn(ex[1]);
+}
+
+// FP32 sigma entry from two-float velocities (isotropic |dq| only), with a rigorous bound; entries whose
+// relation to sigma_min is not settled in FP32 fall back to the exact FP64 entry.
+__device__ __forceinline__ void sigma_entry_f32(const RatesArgs& a, const float* vlh, const float* vll, float s,
+                                                const float* v3h, const float* v3l, const double* vl64,
+                                                const double* v364, float2* pm, float* inv) {
+  float d[3];
+  float v1n = 0.f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float h, e;
+    two_sum(s * vlh[c], -v3h[c], h, e);
+    d[c] = h + (e + (s * vll[c] - v3l[c]));
+    v1n += fabsf(vlh[c]) + fabsf(v3h[c]);
+  }
+  const float sbdq = (float)(a.sb * a.dq);
+  const float sig = sbdq * sqrtf(fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2])));
+  const float E = kRelS * sig + kAbsV * sbdq * v1n;
+  const float smin = (float)a.sigma_min;
+  const float window = (float)a.window;
+  if (sig - E > 2.0f * smin) {
+    const float P = window * sig;
+    *pm = make_float2(P, window * E + kRelP * P);
+    *inv = 1.0f / sig;
+  } else if (sig + E < 0.5f * smin) {
+    const float P = __double2float_rn(a.window * a.sigma_min);
+    *pm = make_float2(P, kRelP * P);
+    *inv = -1.0f;
+  } else {
+    double ex[2];
+    sigma_entry(a, vl64, (double)s, v364, ex);
+    sigma_f_from_exact(ex, pm, inv);
+  }
+}
+
+// exact FP64 energy mismatch of candidate c (order of the FP64 definition)
+__device__ __forceinline__ double dw_fp64(int c, double w0, double wx, double wy, double w3) {
+  const double first = c < 3 ? wx : wy, second = c < 3 ? wy : wx;
+  const double t1 = (c == 2 || c == 5) ? __dsub_rn(w0, first) : __dadd_rn(w0, first);
+  const double t2 = (c == 0 || c == 3) ? __dadd_rn(t1, second) : __dsub_rn(t1, second);
+  return __dsub_rn(t2, w3);
+}
+
+// largest block of each branch count (J * nb^2 rows, rounded up to warps); two blocks per SM
+__host__ __device__ constexpr int max_threads_for(int nb) { return nb == 3 ? 128 : nb == 6 ? 224 : 160; }
+
+// blocks per SM the register budget is sized for (three FP32 blocks measured 11% faster than two on the
+// diamond 8x8x8 workload despite a few spilled registers)
+#ifndef FP_F32_MIN_BLOCKS
+#define FP_F32_MIN_BLOCKS 3
+#endif
+template <typename R>
+__host__ __device__ constexpr int min_blocks_for() { return sizeof(R) == 4 ? FP_F32_MIN_BLOCKS : 2; }
+
+template <typename R, int NB, int MAXT>
+__global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rates_kernel(RatesArgs a) {
+  constexpr int NB2 = NB * NB, NB3 = NB2 * NB, NA = NB / 3;
+  constexpr bool kF64 = sizeof(R) == 8;
+  using C = Cx<R>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long s_item;
+  const int J = a.J, G = a.G, nT = a.nT, N = a.N;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int rows = J * NB2;
+  const Carve cv = make_carve(NB, J, G, a.nquart, nT, nthr);
+  C* cx = reinterpret_cast<C*>(smem);
+  C* sE0 = cx + cv.E0;
+  C* sE1 = cx + cv.E1;
+  C* sE2 = cx + cv.E2;
+  C* sE3 = cx + cv.E3;
+  C* sPsi = cx + cv.Psi;
+  C* sT = cx + cv.T;
+  C* sTw2 = cx + cv.Tw2;
+  C* sTwQ = cx + cv.TwQ;
+  double* db = reinterpret_cast<double*>(cx + cv.ncx);
+  double* sOm0 = db + cv.Om0;
+  double* sOm1 = db + cv.Om1;
+  double* sOm2 = db + cv.Om2;
+  double* sOm3 = db + cv.Om3;
+  double* sV1 = db + cv.V1;
+  double* sV2 = db + cv.V2;
+  double* sV3 = db + cv.V3;
+  double* sSig = db + cv.Sig;
+  double* sW0 = db + cv.W0;
+  double* sW1 = db + cv.W1;
+  double* sW2 = db + cv.W2;
+  double* sW3 = db + cv.W3;
+  double* sRed = db + cv.Red;
+  float* fb = reinterpret_cast<float*>(db + cv.ndbl);
+  float* sHq = fb + cv.Hq;
+  float* sLq = fb + cv.Lq;
+  float* sH1 = fb + cv.H1;
+  float* sL1 = fb + cv.L1;
+  float* sH2 = fb + cv.H2;
+  float* sL2 = fb + cv.L2;
+  float* sH3 = fb + cv.H3;
+  float* sL3 = fb + cv.L3;
+  float* sVH1 = fb + cv.VH1;
+  float* sVL1 = fb + cv.VL1;
+  float* sVH2 = fb + cv.VH2;
+  float* sVL2 = fb + cv.VL2;
+  float* sVH3 = fb + cv.VH3;
+  float* sVL3 = fb + cv.VL3;
+  float2* sSigPM = reinterpret_cast<float2*>(fb + cv.Sigf);  // [4][NB][NB] (P~, margin)
+  float* sSigI = fb + cv.Sigf + 8 * NB2;                      // [4][NB][NB] 1/sigma~ (-1: delta := 1)
+  float* sF0 = fb + cv.F0;
+  float* sF1 = fb + cv.F1;
+  float* sF2 = fb + cv.F2;
+  float* sF3 = fb + cv.F3;
+  int* ib = reinterpret_cast<int*>(fb + cv.nflt);
+  int* sKLs = ib + cv.KL;            // [NA*NA + 1]
+  int* sKLg = sKLs + NA * NA + 1;    // [G]
+  unsigned char* sMask = reinterpret_cast<unsigned char*>(ib + cv.nint);
+
+  // the row this thread owns in the contraction and screening phases
+  const bool has_row = tid < rows;
+  const int rjj = tid / NB2, rj1 = (tid / NB) % NB, rc = tid % NB;
+  const size_t NM = (size_t)N * NB;
+  const bool f32_sigma = !kF64 && a.dq_mode == 0;
+  unsigned long long cnt0 = 0, cnt1 = 0, cnt2 = 0;
+
+  for (int o = tid; o < NA * NA + 1; o += nthr) sKLs[o] = a.kl_start[o];
+  for (int o = tid; o < G; o += nthr) sKLg[o] = a.kl_grp[o];
+
+  for (;;) {
+    if (tid == 0) s_item = (long long)atomicAdd(a.counter, 1ULL);
+    __syncthreads();
+    const long long item = s_item;
+    if (item >= a.n_items) break;
+    const int chunk = (int)(item % a.nchunk);
+    const long long rest = item / a.nchunk;
+    const int qi = (int)(rest % a.nq_sel);
+    const int tile = (int)(rest / a.nq_sel);
+    const int q = a.q_begin + qi;
+    const int j0b = chunk * J;
+    const int g[3] = {q / (a.grid[1] * a.grid[2]), (q / a.grid[2]) % a.grid[1], q % a.grid[2]};
+
+    for (int o = tid; o < J * NB; o += nthr) sE0[o] = ld_e<R>(a, ((size_t)q * NB + j0b) * NB + o);
+    for (int jj = tid; jj < J; jj += nthr) {
+      const int m = q * NB + j0b + jj;
+      const double w = a.omega[m];
+      sOm0[jj] = w;
+      sHq[jj] = a.omh[m];
+      sLq[jj] = a.oml[m];
+      sMask[jj] = (w > 0.0 && (a.mask == nullptr || a.mask[m])) ? 1 : 0;
+    }
+    for (int o = tid; o < nT * J; o += nthr) {
+      const int it = o / J, jj = o % J;
+      const size_t idx = 3 * ((size_t)it * NM + (size_t)q * NB + j0b + jj);
+      if (kF64)
+        sW0[o] = a.wt[idx];
+      else
+        sF0[o] = a.wtf[idx];
+    }
+    __syncthreads();
+    int any = 0;
+    for (int jj = 0; jj < J; ++jj) any |= sMask[jj];
+    const bool active = has_row && sMask[rjj];
+
+    double acc[MAXT];
+    float acch[MAXT], accl[MAXT];
+#pragma unroll
+    for (int t = 0; t < MAXT; ++t) {
+      acc[t] = 0.0;
+      acch[t] = 0.f;
+      accl[t] = 0.f;
+    }
+
+    const int k1_begin = tile * a.t1;
+    const int k1_end = min(N, k1_begin + a.t1);
+    for (int k1 = any ? k1_begin : k1_end; k1 < k1_end; ++k1) {
+      const int g1[3] = {k1 / (a.grid[1] * a.grid[2]), (k1 / a.grid[2]) % a.grid[1], k1 % a.grid[2]};
+      for (int o = tid; o < NB2; o += nthr) sE1[o] = ld_e<R>(a, (size_t)k1 * NB2 + o);
+      for (int o = tid; o < NB; o += nthr) {
+        sOm1[o] = a.omega[k1 * NB + o];
+        sH1[o] = a.omh[k1 * NB + o];
+        sL1[o] = a.oml[k1 * NB + o];
+      }
+      for (int o = tid; o < 3 * NB; o += nthr) {
+        sV1[o] = a.vel[(size_t)k1 * NB * 3 + o];
+        sVH1[o] = a.velh[(size_t)k1 * NB * 3 + o];
+        sVL1[o] = a.vell[(size_t)k1 * NB * 3 + o];
+      }
+      for (int o = tid; o < nT * NB; o += nthr) {
+        const int it = o / NB, j = o % NB;
+        const size_t idx = 3 * ((size_t)it * NM + (size_t)k1 * NB + j);
+        if (kF64) {
+          sW1[2 * o] = a.wt[idx + 1];
+          sW1[2 * o + 1] = a.wt[idx + 2];
+        } else {
+          sF1[2 * o] = a.wtf[idx + 1];
+          sF1[2 * o + 1] = a.wtf[idx + 2];
+        }
+      }
+      for (int Q = tid; Q < a.nquart; Q += nthr) {
+        const int* m = a.qmeta + 9 * Q;
+        long long e = 0;
+        for (int d = 0; d < 3; ++d)
+          e += (long long)a.Lfac[d] * wrapi(g1[d] * m[3 + d] - (g[d] + g1[d]) * m[6 + d], a.grid[d]);
+        sTwQ[Q] = ld_tw<R>(a, (int)(e % a.L));
+      }
+      __syncthreads();
+      // Psi[jj][j1][grp][gt]
+      const int npsi = J * NB * G * 9;
+      for (int o = tid; o < npsi; o += nthr) {
+        const int gt = o % 9;
+        const int t9 = o / 9;
+        const int grp = t9 % G;
+        const int jr = t9 / G;  // jj * NB + j1
+        const int j1 = jr % NB, jj = jr / NB;
+        C sum = cmk<R>(0, 0);
+        for (int qq = a.grp_qstart[grp]; qq < a.grp_qstart[grp + 1]; ++qq) {
+          const int Q = a.grp_q[qq];
+          const int ia = a.qmeta[9 * Q], ja = a.qmeta[9 * Q + 1];
+          const size_t fo = 81 * (size_t)Q + gt;
+          C s = cmk<R>(0, 0);
+#pragma unroll
+          for (int al = 0; al < 3; ++al) {
+            const C e0 = sE0[jj * NB + 3 * ia + al];
+#pragma unroll
+            for (int be = 0; be < 3; ++be) {
+              const C p = cmul(e0, sE1[j1 * NB + 3 * ja + be]);
+              const R fv = ld_fc<R>(a, fo + (al * 3 + be) * 9);
+              s.re = fma(fv, p.re, s.re);
+              s.im = fma(fv, p.im, s.im);
+            }
+          }
+          cfma(sum, sTwQ[Q], s);
+        }
+        sPsi[o] = sum;
+      }
+      __syncthreads();
+
+      for (int k2 = k1; k2 < N; ++k2) {
+        // ---- phase 1: per-k2 tables
+        const int g2[3] = {k2 / (a.grid[1] * a.grid[2]), (k2 / a.grid[2]) % a.grid[1], k2 % a.grid[2]};
+        const int g3[3] = {(g[0] + g1[0] + g2[0]) % a.grid[0], (g[1] + g1[1] + g2[1]) % a.grid[1],
+                           (g[2] + g1[2] + g2[2]) % a.grid[2]};
+        const int k3 = (g3[0] * a.grid[1] + g3[1]) * a.grid[2] + g3[2];
+        for (int o = tid; o < NB2; o += nthr) {
+          sE2[o] = ld_e<R>(a, (size_t)k2 * NB2 + o);
+          sE3[o] = ld_e<R>(a, (size_t)k3 * NB2 + o);
+        }
+        for (int o = tid; o < NB; o += nthr) {
+          sOm2[o] = a.omega[k2 * NB + o];
+          sOm3[o] = a.omega[k3 * NB + o];
+          sH2[o] = a.omh[k2 * NB + o];
+          sL2[o] = a.oml[k2 * NB + o];
+          sH3[o] = a.omh[k3 * NB + o];
+          sL3[o] = a.oml[k3 * NB + o];
+        }
+        for (int o = tid; o < 3 * NB; o += nthr) {
+          sV2[o] = a.vel[(size_t)k2 * NB * 3 + o];
+          sV3[o] = a.vel[(size_t)k3 * NB * 3 + o];
+          if (!kF64) {
+            sVH2[o] = a.velh[(size_t)k2 * NB * 3 + o];
+            sVL2[o] = a.vell[(size_t)k2 * NB * 3 + o];
+            sVH3[o] = a.velh[(size_t)k3 * NB * 3 + o];
+            sVL3[o] = a.vell[(size_t)k3 * NB * 3 + o];
+          }
+        }
+        for (int o = tid; o < nT * NB; o += nthr) {
+          const int it = o / NB, j = o % NB;
+          const size_t i2 = 3 * ((size_t)it * NM + (size_t)k2 * NB + j);
+          const size_t i3 = 3 * ((size_t)it * NM + (size_t)k3 * NB + j);
+          if (kF64) {
+            sW2[2 * o] = a.wt[i2 + 1];
+            sW2[2 * o + 1] = a.wt[i2 + 2];
+            sW3[o] = a.wt[i3 + 2];
+          } else {
+            sF2[2 * o] = a.wtf[i2 + 1];
+            sF2[2 * o + 1] = a.wtf[i2 + 2];
+            sF3[o] = a.wtf[i3 + 2];
+          }
+        }
+        for (int gi = tid; gi < G; gi += nthr) {
+          const int* gm = a.gmeta + 5 * gi;
+          long long e = 0;
+          for (int d = 0; d < 3; ++d) e += (long long)a.Lfac[d] * wrapi(g2[d] * gm[2 + d], a.grid[d]);
+          sTw2[gi] = ld_tw<R>(a, (int)(e % a.L));
+        }
+        __syncthreads();
+        // ---- phase 2: sigma tables; A row and T row
+        // sigma tables [tab][u][j3]: tab 0: v(k2,u)-v3, 1: -v(k2,u)-v3, 2: v(k1,u)-v3, 3: -v(k1,u)-v3
+        for (int o = tid; o < 4 * NB2; o += nthr) {
+          const int tab = o / NB2, u = (o / NB) % NB, j3 = o % NB;
+          const double* vl = (tab < 2 ? sV2 : sV1) + 3 * u;
+          const float sgn = (tab & 1) ? -1.0f : 1.0f;
+          if (f32_sigma) {
+            const float* vlh = (tab < 2 ? sVH2 : sVH1) + 3 * u;
+            const float* vll = (tab < 2 ? sVL2 : sVL1) + 3 * u;
+            sigma_entry_f32(a, vlh, vll, sgn, sVH3 + 3 * j3, sVL3 + 3 * j3, vl, sV3 + 3 * j3, sSigPM + o, sSigI + o);
+          } else {
+            sigma_entry(a, vl, (double)sgn, sV3 + 3 * j3, sSig + 2 * o);
+            sigma_f_from_exact(sSig + 2 * o, sSigPM + o, sSigI + o);
+          }
+        }
+        if (has_row) {
+          // A row (jj, j1 = rj1, c = rc): d = (l, theta)
+          C Arow[NB];
+#pragma unroll
+          for (int d = 0; d < NB; ++d) Arow[d] = cmk<R>(0, 0);
+          const int ka = rc / 3, ga = rc % 3;
+          const C* psi_row = sPsi + (size_t)(rjj * NB + rj1) * G * 9 + ga * 3;
+#pragma unroll
+          for (int la = 0; la < NA; ++la) {
+            const int kl = ka * NA + la;
+            for (int gi = sKLs[kl]; gi < sKLs[kl + 1]; ++gi) {
+              const int grp = sKLg[gi];
+              const C tw = sTw2[grp];
+              const C* ps = psi_row + grp * 9;
+#pragma unroll
+              for (int th = 0; th < 3; ++th) cfma(Arow[3 * la + th], tw, ps[th]);
+            }
+          }
+          C* trow = sT + (size_t)(rjj * NB + rj1) * (NB2 + 1) + rc * NB;
+#pragma unroll
+          for (int j3 = 0; j3 < NB; ++j3) {
+            C s = cmk<R>(0, 0);
+#pragma unroll
+            for (int d = 0; d < NB; ++d) cfma_conj(s, Arow[d], sE3[j3 * NB + d]);
+            trow[j3] = s;
+          }
+        }
+        __syncthreads();
+        // ---- phase 3: W row (jj, x, y) in registers, then window, Gaussian and Bose weights
+        if (active) {
+          const int x = rj1, y = rc;
+          const double w0 = sOm0[rjj];
+          const float h0 = sHq[rjj], l0 = sLq[rjj];
+          const float hx = sH1[x], hy = sH2[y];
+          // candidates 0..2: ordering A (q' = (k1,x), q'' = (k2,y)) ++, +-, --; 3..5: ordering B, swapped
+          const unsigned cand = (k1 != k2) ? 0x3Fu : 0x07u;
+          if (hx != 0.f && hy != 0.f) {
+            C e2row[NB];
+#pragma unroll
+            for (int c = 0; c < NB; ++c) e2row[c] = sE2[y * NB + c];
+            const C* tb = sT + (size_t)(rjj * NB + x) * (NB2 + 1);
+            const float ap = h0 + hx, am = h0 - hx, bp = h0 + hy, bm = h0 - hy;
+            const float apy = ap + hy, apm = ap - hy, amm = am - hy;
+            const float bpx = bp + hx, bpm = bp - hx, bmm = bm - hx;
+            const float s0 = (h0 + hx) + hy;
+            const float2* PA0 = sSigPM + 0 * NB2 + y * NB;
+            const float2* PA1 = sSigPM + 1 * NB2 + y * NB;
+            const float2* PB0 = sSigPM + 2 * NB2 + x * NB;
+            const float2* PB1 = sSigPM + 3 * NB2 + x * NB;
+#pragma unroll 1
+            for (int j3 = 0; j3 < NB; ++j3) {
+              const float h3 = sH3[j3];
+              if (h3 == 0.f) continue;
+              const float sS = kRelS * (s0 + h3);
+              const float2 a0 = PA0[j3], a1 = PA1[j3], b0 = PB0[j3], b1 = PB1[j3];
+              unsigned accm = 0, band = 0;
+              // accept when |dw~| < P - M, reject when |dw~| > P + M, else decide in FP64
+#define FP_SCREEN(c, dv, pm)                                             \
+  {                                                                      \
+    const float M_ = sS + (pm).y, ad_ = fabsf(dv);                       \
+    accm |= (ad_ < (pm).x - M_ ? 1u : 0u) << (c);                        \
+    band |= (ad_ <= (pm).x + M_ && !(ad_ < (pm).x - M_) ? 1u : 0u) << (c); \
+  }
+              FP_SCREEN(0, apy - h3, a0)
+              FP_SCREEN(1, apm - h3, a1)
+              FP_SCREEN(2, amm - h3, a1)
+              FP_SCREEN(3, bpx - h3, b0)
+              FP_SCREEN(4, bpm - h3, b1)
+              FP_SCREEN(5, bmm - h3, b1)
+#undef FP_SCREEN
+              accm &= cand;
+              band &= cand;
+              while (band) {
+                const int c = __ffs(band) - 1;
+                band &= band - 1;
+                const int tab = (c < 3) ? (c == 0 ? 0 : 1) : (c == 3 ? 2 : 3);
+                const int ent = tab * NB2 + ((c < 3) ? y : x) * NB + j3;
+                const double d64 = dw_fp64(c, w0, sOm1[x], sOm2[y], sOm3[j3]);
+                double P64;
+                if (kF64 || !f32_sigma) {
+                  P64 = sSig[2 * ent];
+                } else {
+                  double ex[2];
+                  const double* vl = ((tab < 2) ? sV2 + 3 * y : sV1 + 3 * x);
+                  sigma_entry(a, vl, (tab & 1) ? -1.0 : 1.0, sV3 + 3 * j3, ex);
+                  P64 = ex[0];
+                }
+                if (fabs(d64) <= P64) accm |= 1u << c;
+              }
+              if (!accm) continue;
+              C Wv = cmk<R>(0, 0);
+#pragma unroll
+              for (int c = 0; c < NB; ++c) cfma(Wv, e2row[c], tb[c * NB + j3]);
+              while (accm) {
+                const int c = __ffs(accm) - 1;
+                accm &= accm - 1;
+                const int p = c % 3;
+                cnt0 += (p == 0);
+                cnt1 += (p == 1);
+                cnt2 += (p == 2);
+                const bool ordA = c < 3;
+                const int tab = (c < 3) ? (c == 0 ? 0 : 1) : (c == 3 ? 2 : 3);
+                const int ent = tab * NB2 + (ordA ? y : x) * NB + j3;
+                // Bose selectors: leg q' takes (1+n)/w unless --, leg q'' takes (1+n)/w only for ++
+                const int s1 = (p == 2) ? 1 : 0, s2 = (p == 0) ? 0 : 1;
+                const int i1 = ordA ? x : y, i2 = ordA ? y : x;
+                if constexpr (kF64) {
+                  const double W2 = Wv.re * Wv.re + Wv.im * Wv.im;
+                  const double d64 = dw_fp64(c, w0, sOm1[x], sOm2[y], sOm3[j3]);
+                  const double inv = sSig[2 * ent + 1];
+                  double delta = 1.0;
+                  if (inv >= 0.0) {
+                    const double xx = d64 * inv;
+                    delta = exp(-xx * xx) * inv * kInvSqrtPi;
+                  }
+                  const double base = (p == 2 ? (1.0 / 6.0) : 0.5) * W2 * delta;
+                  const double* wq1 = ordA ? sW1 : sW2;
+                  const double* wq2 = ordA ? sW2 : sW1;
+#pragma unroll
+                  for (int t = 0; t < MAXT; ++t) {
+                    if (t >= nT) break;
+                    acc[t] += base * sW0[t * J + rjj] * wq1[2 * (t * NB + i1) + s1] * wq2[2 * (t * NB + i2) + s2] *
+                              sW3[t * NB + j3];
+                  }
+                } else {
+                  const float W2 = Wv.re * Wv.re + Wv.im * Wv.im;
+                  // dw from two-float frequencies with error-free sums
+                  const float fh = ordA ? hx : hy, fl = ordA ? sL1[x] : sL2[y];
+                  const float sh = ordA ? hy : hx, sl = ordA ? sL2[y] : sL1[x];
+                  const float sg1 = (p == 2) ? -1.f : 1.f, sg2 = (p == 0) ? 1.f : -1.f;
+                  float t0, e1, e2, e3;
+                  two_sum(h0, sg1 * fh, t0, e1);
+                  two_sum(t0, sg2 * sh, t0, e2);
+                  two_sum(t0, -h3, t0, e3);
+                  const float lo = (((l0 + sg1 * fl) + sg2 * sl) - sL3[j3]) + ((e1 + e2) + e3);
+                  const float dwf = t0 + lo;
+                  const float inv = sSigI[ent];
+                  float delta = 1.0f;
+                  if (inv >= 0.f) {
+                    const float xx = dwf * inv;
+                    delta = __expf(-xx * xx) * inv * (float)kInvSqrtPi;
+                  }
+                  const float base = ((p == 2) ? (1.0f / 6.0f) : 0.5f) * W2 * delta;
+                  const float* fq1 = ordA ? sF1 : sF2;
+                  const float* fq2 = ordA ? sF2 : sF1;
+#pragma unroll
+                  for (int t = 0; t < MAXT; ++t) {
+                    if (t >= nT) break;
+                    const float term = base * sF0[t * J + rjj] * fq1[2 * (t * NB + i1) + s1] *
+                                       fq2[2 * (t * NB + i2) + s2] * sF3[t * NB + j3];
+                    float s, e;
+                    two_sum(acch[t], term, s, e);
+                    acch[t] = s;
+                    accl[t] += e;
+                  }
+                }
+              }
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // deterministic reduction: per-row sums in shared memory, then rows of each j0 in order
+    if (has_row) {
+#pragma unroll
+      for (int t = 0; t < MAXT; ++t) {
+        if (t >= nT) break;
+        sRed[(size_t)tid * nT + t] = kF64 ? acc[t] : (double)acch[t] + (double)accl[t];
+      }
+    }
+    __syncthreads();
+    for (int o = tid; o < J * nT; o += nthr) {
+      const int jj = o / nT, t = o % nT;
+      double s = 0.0;
+      for (int r = 0; r < NB2; ++r) s += sRed[(size_t)(jj * NB2 + r) * nT + t];
+      a.partial[(size_t)item * J * nT + o] = s;
+    }
+    __syncthreads();
+  }
+  // accepted counts
+  for (int off = 16; off > 0; off >>= 1) {
+    cnt0 += __shfl_down_sync(0xffffffffu, cnt0, off);
+    cnt1 += __shfl_down_sync(0xffffffffu, cnt1, off);
+    cnt2 += __shfl_down_sync(0xffffffffu, cnt2, off);
+  }
+  if ((tid & 31) == 0) {
+    if (cnt0) atomicAdd(a.counts + 0, cnt0);
+    if (cnt1) atomicAdd(a.counts + 1, cnt1);
+    if (cnt2) atomicAdd(a.counts + 2, cnt2);
+  }
+}
+
+}  // namespace
+}  // namespace fp

@@ -77,7 +77,7 @@ def test_fp64_parity_workload1_full_grid(lib):
 
 
 @pytest.mark.parametrize("tiles", [dict(block_j0=1, k1_tile=3, threads=64), dict(block_j0=3, k1_tile=7, threads=96),
-                                   dict(block_j0=3, k1_tile=64, threads=384)])
+                                   dict(block_j0=3, k1_tile=64, threads=128)])
 def test_fp64_tilings_agree(lib, tiles):
     cr = synth.simple_cubic((4, 3, 3))
     w, e, v = oracle_modes(cr)
@@ -150,3 +150,23 @@ def test_workload2_full_size_sampled_modes(lib):
     sel = np.sort(rng.choice(np.arange(cr.nb, cr.nq * cr.nb), size=3, replace=False))
     ref, _ = oracle.rates4(cr, w, e, v, sel=sel)
     compare(out.reshape(1, -1)[:, sel], ref, RTOL_FP64)
+
+
+def test_autotuned_tiles_and_graph_replay(lib):
+    """fp_autotune picks admissible tiles; tuned and graph-replayed calls keep FP64 parity."""
+    cr = synth.diamond_si((4, 4, 3))
+    w, e, v = oracle_modes(cr)
+    ref, acc = oracle.rates4(cr, w, e, v)
+    with lib.Context.from_crystal(cr) as ctx:
+        ctx.set_modes(w, e, v)
+        tiles, best = ctx.autotune(cr.temps, cr.scalebroad, precision=FP_PREC_FP64)
+        assert cr.nb % tiles["block_j0"] == 0 and tiles["threads"] >= tiles["block_j0"] * cr.nb ** 2 and best > 0
+        outs = []
+        for _ in range(3):  # first call captures the graph, the others replay it
+            out, st = ctx.rates4(cr.temps, cr.scalebroad)
+            assert st["tile"][0] == tiles["block_j0"]
+            outs.append(out)
+        plain, _ = ctx.rates4(cr.temps, cr.scalebroad, no_graph=1)
+    for out in outs + [plain]:
+        compare(out.reshape(1, -1), ref, RTOL_FP64)
+    assert np.array_equal(outs[0], outs[2]) and np.array_equal(outs[0], plain)

@@ -1,0 +1,141 @@
+"""Surrogate path on the GPU: phase-space features vs the oracle, network gradients vs the FP64
+oracle backward pass, and the fitted surrogate vs exact rates (accuracy, exact fallback, and what
+it saves)."""
+import ctypes
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.mlp as omlp
+from paper_2104_04895_gb300 import synth
+
+from conftest import oracle_modes
+
+pytestmark = pytest.mark.gpu
+
+
+class SurOpts(ctypes.Structure):
+    _fields_ = [("train_frac", ctypes.c_double), ("holdout_frac", ctypes.c_double), ("tol", ctypes.c_double),
+                ("seed", ctypes.c_ulonglong), ("epochs", ctypes.c_int), ("batch", ctypes.c_int),
+                ("lr", ctypes.c_double), ("precision", ctypes.c_int)]
+
+
+class SurReport(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in ("n_modes", "n_train", "n_holdout", "n_fallback_modes", "n_bins",
+                                            "n_bins_fallback")] + \
+               [(n, ctypes.c_double) for n in ("final_loss", "holdout_median_rel_err", "holdout_p90_rel_err",
+                                               "holdout_max_rel_err", "ms_exact", "ms_features", "ms_train",
+                                               "ms_predict", "ms_fallback", "ms_total")]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2104_04895_gb300 import binding
+    L = binding.load()
+    dp = ctypes.POINTER(ctypes.c_double)
+    fp_ = ctypes.POINTER(ctypes.c_float)
+    L.fp_phase3.argtypes = [ctypes.c_void_p, ctypes.c_int, dp, ctypes.c_double, ctypes.c_void_p, dp, dp]
+    L.fp_mlp_params_size.argtypes = [ctypes.c_int]
+    L.fp_mlp_loss_grad.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, fp_, fp_, fp_, fp_, fp_]
+    L.fp_surrogate_default_opts.argtypes = [ctypes.POINTER(SurOpts)]
+    L.fp_surrogate_default_opts.restype = None
+    L.fp_surrogate_fit.argtypes = [ctypes.c_void_p, ctypes.c_int, dp, ctypes.c_double, ctypes.POINTER(SurOpts),
+                                   ctypes.POINTER(SurReport)]
+    L.fp_surrogate_rates.argtypes = [ctypes.c_void_p, dp, ctypes.POINTER(ctypes.c_ubyte)]
+    return binding
+
+
+def _d(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+@pytest.mark.parametrize("maker", [lambda: synth.workload(1), lambda: synth.diamond_si((3, 3, 2)),
+                                   lambda: synth.licoo2((3, 3, 2))])
+def test_phase3_matches_oracle(lib, maker):
+    cr = maker()
+    w, e, v = oracle_modes(cr)
+    temps = np.array([300.0, 700.0])
+    p_ref, wp_ref = oracle.phase3(cr, w, v, temps=temps)
+    with lib.Context.from_crystal(cr) as ctx:
+        ctx.set_modes(w, e, v)
+        p = np.zeros(cr.nq * cr.nb)
+        wp = np.zeros((2, cr.nq * cr.nb))
+        rc = ctx.L.fp_phase3(ctx.h, 2, _d(temps), cr.scalebroad, None, _d(p), _d(wp))
+        assert rc == 0
+    nz = p_ref != 0
+    assert nz.any()
+    assert np.all(p[~nz] == 0)
+    assert np.max(np.abs(p[nz] - p_ref[nz]) / p_ref[nz]) <= 1e-10
+    nz = wp_ref != 0
+    assert np.all(wp[~nz] == 0)
+    assert np.max(np.abs(wp[nz] - wp_ref[nz]) / np.abs(wp_ref[nz])) <= 1e-10
+
+
+def test_network_gradient_matches_fp64_oracle(lib):
+    F, B = 12, 96
+    rng = np.random.Generator(np.random.PCG64(21))
+    p = omlp.init_params(F, seed=4) + 0.02 * rng.normal(size=omlp.n_params(F))
+    X = rng.normal(size=(B, F))
+    y = rng.normal(size=B)
+    loss_ref, g_ref = omlp.loss_and_grad(p, X, y, F)
+    L = lib.load()
+    assert L.fp_mlp_params_size(F) == p.size
+    pf = p.astype(np.float32)
+    Xf = X.astype(np.float32)
+    yf = y.astype(np.float32)
+    g = np.zeros(p.size, np.float32)
+    loss = np.zeros(1, np.float32)
+    assert L.fp_mlp_loss_grad(0, F, B, _f(Xf), _f(yf), _f(pf), _f(g), _f(loss)) == 0
+    # FP32 kernels vs the FP64 oracle on FP32-rounded inputs
+    loss_r, g_r = omlp.loss_and_grad(pf.astype(np.float64), Xf.astype(np.float64), yf.astype(np.float64), F)
+    assert loss[0] == pytest.approx(loss_r, rel=1e-5)
+    assert np.max(np.abs(g - g_r)) <= 1e-4 * np.max(np.abs(g_r))
+    # and the gradient is that of the FP64 definition up to the FP32 rounding of the inputs
+    assert np.max(np.abs(g - g_ref)) <= 2e-3 * np.max(np.abs(g_ref))
+
+
+def test_surrogate_fit_accuracy_fallback_and_savings(lib):
+    cr = synth.diamond_si((8, 8, 8))
+    temps = np.array([300.0, 500.0, 700.0, 900.0])
+    L = lib.load()
+    with lib.Context.from_crystal(cr) as ctx:
+        ctx.modes(copy=False)
+        t0 = time.perf_counter()
+        exact, st = ctx.rates4(temps, cr.scalebroad, precision=lib.FP_PREC_MIXED)
+        t_exact = time.perf_counter() - t0
+        so = SurOpts()
+        L.fp_surrogate_default_opts(ctypes.byref(so))
+        rep = SurReport()
+        t0 = time.perf_counter()
+        assert L.fp_surrogate_fit(ctx.h, len(temps), _d(temps), cr.scalebroad, ctypes.byref(so),
+                                  ctypes.byref(rep)) == 0
+        t_sur = time.perf_counter() - t0
+        rates = np.zeros_like(exact)
+        used = np.zeros(exact.shape, np.uint8)
+        assert L.fp_surrogate_rates(ctx.h, _d(rates), used.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))) == 0
+    ex = exact.reshape(len(temps), -1)
+    ra = rates.reshape(len(temps), -1)
+    us = used.reshape(len(temps), -1).astype(bool)
+    # exact entries are the exact rates, bit for bit
+    assert np.array_equal(ra[us], ex[us])
+    pred = (~us) & (ex > 0)
+    rel = np.abs(ra[pred] - ex[pred]) / ex[pred]
+    frac_exact = us[:, ex[0] > 0].mean() if (ex[0] > 0).any() else 1.0
+    print(f"surrogate: {rep.n_train} train, {rep.n_holdout} held-out, {rep.n_fallback_modes} fallback modes; "
+          f"{rep.n_bins_fallback}/{rep.n_bins} bins exact; exact share {frac_exact:.3f}; predicted median rel err "
+          f"{np.median(rel) if rel.size else 0:.4f} p90 {np.quantile(rel, 0.9) if rel.size else 0:.4f}; "
+          f"held-out median {rep.holdout_median_rel_err:.4f}; loss {rep.final_loss:.2e}; times exact "
+          f"{t_exact:.3f}s surrogate {t_sur:.3f}s (exact part {rep.ms_exact + rep.ms_fallback:.0f} ms, "
+          f"train {rep.ms_train:.0f} ms)")
+    assert rep.n_train > 0 and rep.n_holdout > 0
+    if rel.size:
+        # bins kept on the network were judged below the 5% tolerance on held-out modes
+        assert np.median(rel) <= 0.05
+    # the network replaces exact evaluation for part of the grid
+    assert frac_exact < 1.0

@@ -63,7 +63,7 @@ def test_noalloc_rejects_problems_beyond_the_static_scratch():
     from paper_2104_04895_gb300 import binding
     L, f = _entry(binding)
     cr = synth.licoo2((16, 16, 16))
-    temps = np.linspace(300.0, 1000.0, 16)
+    temps = np.linspace(300.0, 1000.0, 8)
     with binding.Context.from_crystal(cr) as ctx:
         ctx.modes(copy=False)
         out = torch.zeros(len(temps) * cr.nq * cr.nb, dtype=torch.float64, device="cuda")
