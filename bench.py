@@ -49,6 +49,10 @@ def parse():
     p.add_argument("--no-other", action="store_true", help="skip timing the other precision")
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--surrogate", action="store_true", help="learned-rate study instead of the bench line")
+    p.add_argument("--configs", action="store_true",
+                   help="per-workload study: time and oracle error of both precisions on workloads 1-5")
+    p.add_argument("--budget-s", type=float, default=60.0,
+                   help="--configs: per-precision time budget; larger rate sets are timed on a q-range")
     p.add_argument("--seed", type=int, default=2104)
     p.add_argument("--grid", type=int, nargs=3, default=None,
                    help="override the workload's q-grid (small profiling cases only; not a bench line)")
@@ -207,6 +211,8 @@ def main():
         return run_reference(args)
     if args.surrogate:
         return run_surrogate(args)
+    if args.configs:
+        return run_configs(args)
     import torch
     import torch.distributed as dist
     from paper_2104_04895_gb300 import binding
@@ -356,6 +362,55 @@ def run_surrogate(args):
                                   "max": float(rel.max()) if rel.size else None},
             "report": rep}
     print(json.dumps(line), flush=True)
+
+
+def run_configs(args):
+    """One JSON line per workload: seconds per full-grid rate set (measured, or extrapolated from a timed
+    q-range when a full set would exceed the budget), process-terms/s and the oracle error on sampled modes."""
+    import oracle
+    from paper_2104_04895_gb300 import binding
+    for wl in (1, 2, 3, 4, 5):
+        cr = synth.workload(wl)
+        N, nb = cr.nq, cr.nb
+        cands = 3.0 * N ** 3 * nb ** 4
+        res = {"workload": synth.WORKLOAD_NAMES[wl], "candidates": cands}
+        with binding.Context.from_crystal(cr) as ctx:
+            w, e, v = ctx.modes()
+            ctx.autotune(cr.temps, cr.scalebroad, precision=binding.FP_PREC_MIXED)
+            rng = np.random.Generator(np.random.PCG64(77 + wl))
+            sel = [int(m) for m in rng.choice(np.arange(nb, N * nb), size=1, replace=False)]
+            q_s = sel[0] // nb
+            ref = None
+            # the oracle costs ~3 N^2 nb^3 / 2e7 s per mode on 16 cores: skip it beyond ~2 minutes
+            if 3.0 * N ** 2 * nb ** 3 <= 2.5e9:
+                t0 = time.perf_counter()
+                ref, _ = oracle.rates4(cr, w, e, v, sel=sel, nthreads=os.cpu_count() or 1)
+                t_or = time.perf_counter() - t0
+                res["oracle"] = {"s_per_mode": t_or, "terms_per_s": 3.0 * N ** 2 * nb ** 3 / t_or,
+                                 "cores": os.cpu_count()}
+            vals = {}
+            for name, prec in (("fp64", binding.FP_PREC_FP64), ("mixed", binding.FP_PREC_MIXED)):
+                # probe a q-range to decide between a full run and an extrapolated one
+                nq_probe = max(1, min(N, N // 64))
+                _, st = ctx.rates4(cr.temps, cr.scalebroad, precision=prec, q_begin=0, q_end=nq_probe)
+                est = st["ms"] * 1e-3 * N / nq_probe
+                if est <= args.budget_s:
+                    out, st = ctx.rates4(cr.temps, cr.scalebroad, precision=prec)
+                    secs, how = st["ms"] * 1e-3, "full grid"
+                    val = out.reshape(len(cr.temps), -1)[:, sel]
+                else:
+                    nq = max(1, int(N * args.budget_s / est / 2))
+                    q0 = min(max(0, q_s - nq // 2), N - nq)
+                    out, st = ctx.rates4(cr.temps, cr.scalebroad, precision=prec, q_begin=q0, q_end=q0 + nq)
+                    secs, how = st["ms"] * 1e-3 * N / nq, f"extrapolated from q-range of {nq}/{N} points"
+                    val = out.reshape(len(cr.temps), -1)[:, sel]
+                vals[name] = val
+                err = float(np.max(np.abs(val - ref) / np.abs(ref))) if ref is not None else None
+                res[name] = {"s_per_rate_set": secs, "terms_per_s": cands / secs, "timing": how,
+                             "rel_err_vs_oracle": err, "tile": st["tile"]}
+            res["mixed"]["rel_err_vs_fp64_gpu"] = float(np.max(np.abs(vals["mixed"] - vals["fp64"]) /
+                                                             np.abs(vals["fp64"])))
+        print(json.dumps(res), flush=True)
 
 
 if __name__ == "__main__":

@@ -175,6 +175,15 @@ int fp_rates4_noalloc(fp_ctx* ctx, int nT, const double* T, double scalebroad, c
 int fp_phase3(fp_ctx* ctx, int nT, const double* T, double scalebroad, const fp_rates_opts* opts, double* p3,
               double* wp3);
 
+/*
+ * Four-phonon weighted phase space of every mode: the sum of fp_rates4 with |V|^2 replaced by 1 and without
+ * hbar^2 pi / 8, i.e. (1/N^2) sum over (q', q'') and branch triples of c_p B_p/n delta_p / (w w1 w2 w3)
+ * (Eqs. tao0 and 4phgamma without V4; the paper's WP4 output, Sec. 2.1), estimated from q' on a stride
+ * (stride 1 = the full sum; stride s uses every s-th q' with all q'', scaled by s).  FP32 Gaussian, exact
+ * window decisions.  wp4: host, nT x N x nb.
+ */
+int fp_phase4(fp_ctx* ctx, int nT, const double* T, double scalebroad, int stride, double* wp4);
+
 /* Number of parameters of the surrogate network for n_in input features (3 tanh layers of 128). */
 int fp_mlp_params_size(int n_in);
 
@@ -191,7 +200,7 @@ int fp_mlp_loss_grad(int device, int n_in, int batch, const float* X, const floa
 typedef struct {
   double train_frac;       /* share of positive-frequency modes with exact training rates (0.10) */
   double holdout_frac;     /* share of modes with exact rates that only judge the network (0.05) */
-  double tol;              /* mean held-out relative error above which a bin falls back to exact rates (0.05) */
+  double tol;              /* held-out relative error bound above which a bin falls back to exact rates (0.05) */
   unsigned long long seed; /* seeds the mode subsets, the initial weights and the minibatch order */
   int epochs;              /* Adam epochs (400) */
   int batch;               /* minibatch rows (1024) */
@@ -212,10 +221,11 @@ void fp_surrogate_default_opts(fp_surrogate_opts* opts);
 /*
  * Learned four-phonon rates (the paper has no learned component).  Exact rates (fp_rates4) of a seeded
  * train_frac share of the modes train a 3 x 128 tanh network on the GPU (hand-written forward, backward
- * and Adam kernels) that maps per-mode features (w, |v|, branch, T, n0, P3, WP3, and the q-point as
- * cos/sin(2 pi g_a / N_a)) to log(rate).  Exact
- * rates of a further holdout_frac share judge it per bin (branch x frequency quartile); bins whose mean
- * held-out relative error exceeds tol, and bins without held-out modes, are evaluated exactly.  Every
+ * and Adam kernels) that maps per-mode features (w, |v|, branch, T, n0, P3, WP3, WP4 sampled on every
+ * (N/32)-th q', and the q-point as cos/sin(2 pi g_a / N_a)) to log(rate).  Exact
+ * rates of a further holdout_frac share judge it per bin (branch x frequency quartile); a bin keeps the
+ * network's rates only when it has at least 16 held-out (mode, T) rows and the upper confidence bound of
+ * their mean relative error (mean + 2 standard errors) is within tol; every other bin is evaluated exactly.  Every
  * trained, held-out or fallback mode keeps its exact rate.  Results are read with fp_surrogate_rates.
  */
 int fp_surrogate_fit(fp_ctx* ctx, int nT, const double* T, double scalebroad, const fp_surrogate_opts* opts,

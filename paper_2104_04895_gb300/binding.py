@@ -50,7 +50,7 @@ class fp_stats(ctypes.Structure):
 
 
 EXPORTS = ["fp_version", "fp_default_opts", "fp_init", "fp_set_stream", "fp_modes", "fp_set_modes", "fp_rates4",
-           "fp_rates4_device", "fp_rates4_noalloc", "fp_autotune", "fp_phase3", "fp_mlp_params_size",
+           "fp_rates4_device", "fp_rates4_noalloc", "fp_autotune", "fp_phase3", "fp_phase4", "fp_mlp_params_size",
            "fp_mlp_loss_grad", "fp_surrogate_default_opts", "fp_surrogate_fit", "fp_surrogate_rates", "fp_free",
            "fp_last_error"]
 
@@ -120,6 +120,8 @@ def load(path: str | None = None):
     L.fp_autotune.restype = ctypes.c_int
     L.fp_phase3.argtypes = [vp, ctypes.c_int, dp, ctypes.c_double, ctypes.POINTER(fp_rates_opts), dp, dp]
     L.fp_phase3.restype = ctypes.c_int
+    L.fp_phase4.argtypes = [vp, ctypes.c_int, dp, ctypes.c_double, ctypes.c_int, dp]
+    L.fp_phase4.restype = ctypes.c_int
     L.fp_mlp_params_size.argtypes = [ctypes.c_int]
     L.fp_mlp_params_size.restype = ctypes.c_int
     fpp = ctypes.POINTER(ctypes.c_float)
@@ -290,6 +292,13 @@ class Context:
                                                 _dp(p3), _dp(wp3)))
         del keep
         return p3, wp3
+
+    def phase4(self, temps, scalebroad=1.0, stride=1):
+        """Four-phonon weighted phase space (fp_phase4), (nT, N*nb)."""
+        T = np.ascontiguousarray(temps, np.float64).reshape(-1)
+        wp4 = np.zeros((len(T), self.N * self.nb))
+        _check(self.L, self.h, self.L.fp_phase4(self.h, len(T), _dp(T), float(scalebroad), int(stride), _dp(wp4)))
+        return wp4
 
     def surrogate_fit(self, temps, scalebroad=1.0, **sopts):
         """Learned rates (fp_surrogate_fit); returns the report as a dict."""

@@ -1,6 +1,7 @@
 // C-ABI of libfourphonon: context, validation, device memory, launches (see include/fourphonon.h).
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <numeric>
@@ -28,10 +29,28 @@ int fail(fp_ctx* c, int code, const std::string& msg) {
                   std::string(#call) + ": " + cudaGetErrorString(e_));                       \
   } while (0)
 
+// Host-side fault injection for the allocation path: with FP_FAULT_ALLOC=k in the environment, the k-th
+// device allocation of the context API after the variable was (re)set reports cudaErrorMemoryAllocation
+// without allocating, so callers can test FP_ENOMEM handling without touching the GPU.
+bool injected_alloc_failure() {
+  static std::string last;
+  static long count = 0;
+  const char* env = std::getenv("FP_FAULT_ALLOC");
+  const std::string cur = env ? env : "";
+  if (cur != last) {
+    last = cur;
+    count = 0;
+  }
+  if (cur.empty()) return false;
+  const long k = std::strtol(cur.c_str(), nullptr, 10);
+  return k > 0 && ++count == k;
+}
+
 template <typename T>
 cudaError_t dalloc(T** p, size_t n) {
   *p = nullptr;
   if (n == 0) n = 1;
+  if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
   return cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
 }
 
@@ -177,8 +196,10 @@ int fp_init(fp_ctx** out, const double lattice[9], int natoms, const double* fra
   reciprocal(lattice, c->rec, nullptr);
   c->mass.assign(mass, mass + natoms);
 
+  int* d_atoms4 = nullptr;  // temporary (atoms of each quartet for the mass scaling)
   auto bail = [&](int rc) {
     g_init_error = c->err;
+    if (d_atoms4) cudaFree(d_atoms4);
     fp_free(c);
     return rc;
   };
@@ -273,7 +294,6 @@ int fp_init(fp_ctx** out, const double lattice[9], int natoms, const double* fra
     std::vector<int> fill(kl_start.begin(), kl_start.end() - 1);
     for (int gi = 0; gi < c->G; ++gi) kl_grp[fill[gmeta[5 * gi] * natoms + gmeta[5 * gi + 1]]++] = gi;
   }
-  int* d_atoms4 = nullptr;
   INIT_CUDA(dalloc(&c->d_qmeta, qmeta.size()));
   INIT_CUDA(dalloc(&c->d_qfc, qfc.size()));
   INIT_CUDA(dalloc(&c->d_gmeta, gmeta.size()));

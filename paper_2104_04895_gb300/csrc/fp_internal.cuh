@@ -59,6 +59,8 @@ struct RatesArgs {
   double* partial;           // [n_items][J][nT]
   unsigned long long* counter;
   unsigned long long* counts; // [3]
+  int unit_vertex;           // 1: |W|^2 = 1 (weighted phase space), q' on a stride, ordered (q', q'') pairs
+  int k1_stride;             // q' stride of the unit-vertex mode
 };
 
 // Tile plan of one rates call.
@@ -152,7 +154,11 @@ void scratch_sizes(const fp_ctx* c, const Plan& p, int nT, bool with_mask, size_
 // return the accepted counts.  d_out: nT x N x nb doubles (zeroed here).
 // use_graph: capture the device part once per set of launch parameters and replay it as a CUDA graph.
 int run_rates(fp_ctx* c, const fp_rates_opts& o, const Plan& p, const Scratch& s, int nT, const double* T,
-              double sb, double* d_out, unsigned long long counts[4], bool use_graph, std::string* err);
+              double sb, double* d_out, unsigned long long counts[4], bool use_graph, std::string* err,
+              int unit_stride = 0);
+// Sampled four-phonon weighted phase space of every mode (surrogate feature): the rate sum with |W|^2 = 1
+// over q' on a stride (ordered pairs), scaled to the full grid; d_out: nT x N x nb, mixed precision.
+int phase4_sampled(fp_ctx* c, int nT, const double* T, double sb, int stride, double* d_out, std::string* err);
 void fill_stats(const fp_ctx* c, const fp_rates_opts& o, const Plan& p, const unsigned long long counts[4],
                 fp_stats* st);
 }  // namespace fp

@@ -202,7 +202,8 @@ void scratch_sizes(const fp_ctx* c, const Plan& p, int nT, bool with_mask, size_
 }
 
 int run_rates(fp_ctx* c, const fp_rates_opts& o, const Plan& p, const Scratch& sc, int nT, const double* T,
-              double sb, double* d_out, unsigned long long counts[4], bool use_graph, std::string* err) {
+              double sb, double* d_out, unsigned long long counts[4], bool use_graph, std::string* err,
+              int unit_stride) {
   cudaStream_t s = c->stream;
   const int N = c->N, nb = c->nb;
   const size_t nm = (size_t)N * nb;
@@ -270,10 +271,15 @@ int run_rates(fp_ctx* c, const fp_rates_opts& o, const Plan& p, const Scratch& s
   a.partial = sc.partial;
   a.counter = sc.counters;
   a.counts = sc.counters + 1;
+  a.unit_vertex = unit_stride > 0 ? 1 : 0;
+  a.k1_stride = unit_stride > 0 ? unit_stride : 1;
 
   const int want_f32 = o.precision != FP_PREC_FP64;
   const double conv = kConv;
-  const double pref = kPi * kHbar * kHbar * conv * conv * conv * conv / (8.0 * (double)N * (double)N);
+  // unit-vertex mode: no physical prefactor; scale the strided ordered-pair sum to the full grid
+  const double pref = unit_stride > 0
+                          ? (double)unit_stride / ((double)N * (double)N)
+                          : kPi * kHbar * kHbar * conv * conv * conv * conv / (8.0 * (double)N * (double)N);
   const void* k = rates_kernel_ptr(o.precision, nb, nT);
   // the device part of a rate set: Bose weights, FP32 tables, cleared counters and output, the persistent
   // rate kernel and the reduction
@@ -381,4 +387,51 @@ void fill_stats(const fp_ctx* c, const fp_rates_opts& o, const Plan& p, const un
   st->tile[3] = p.ctas;
 }
 
+}  // namespace fp
+
+namespace fp {
+int phase4_sampled(fp_ctx* c, int nT, const double* T, double sb, int stride, double* d_out, std::string* err) {
+  fp_rates_opts o;
+  fp_default_opts(&o);
+  o.precision = FP_PREC_MIXED;
+  o.no_graph = 1;
+  Plan p;
+  int rc = plan_rates(c, o, nT, 0, &p, err);
+  if (rc) return rc;
+  // a q' tile of one stride: every item owns exactly one sampled q'
+  p.t1 = stride;
+  p.ntile = (c->N + stride - 1) / stride;
+  p.n_items = (long long)p.ntile * p.nq_sel * p.nchunk;
+  if (p.ctas > p.n_items) p.ctas = (int)p.n_items;
+  size_t sz[13], total = 0, off[13];
+  scratch_sizes(c, p, nT, false, sz);
+  for (int i = 0; i < 13; ++i) {
+    off[i] = total;
+    total += sz[i];
+  }
+  unsigned char* b = nullptr;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&b), total);
+  if (e != cudaSuccess) {
+    *err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    return FP_ENOMEM;
+  }
+  Scratch sc;
+  sc.counters = reinterpret_cast<unsigned long long*>(b + off[0]);
+  sc.T = reinterpret_cast<double*>(b + off[1]);
+  sc.mask = nullptr;
+  sc.wt = reinterpret_cast<double*>(b + off[3]);
+  sc.partial = reinterpret_cast<double*>(b + off[4]);
+  sc.omh = reinterpret_cast<float*>(b + off[5]);
+  sc.oml = reinterpret_cast<float*>(b + off[6]);
+  sc.velh = reinterpret_cast<float*>(b + off[7]);
+  sc.vell = reinterpret_cast<float*>(b + off[8]);
+  sc.evf = reinterpret_cast<float2*>(b + off[9]);
+  sc.qfcf = reinterpret_cast<float*>(b + off[10]);
+  sc.twf = reinterpret_cast<float2*>(b + off[11]);
+  sc.wtf = reinterpret_cast<float*>(b + off[12]);
+  unsigned long long counts[4];
+  rc = run_rates(c, o, p, sc, nT, T, sb, d_out, counts, false, err, stride);
+  cudaFree(b);
+  return rc;
+}
 }  // namespace fp

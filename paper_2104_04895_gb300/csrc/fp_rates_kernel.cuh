@@ -390,7 +390,11 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
 
     const int k1_begin = tile * a.t1;
     const int k1_end = min(N, k1_begin + a.t1);
-    for (int k1 = any ? k1_begin : k1_end; k1 < k1_end; ++k1) {
+    // unit-vertex (phase-space) mode: q' on a stride, every q'' in one ordering, |W|^2 = 1
+    const bool unit = a.unit_vertex != 0;
+    const int k1_first = unit ? ((k1_begin + a.k1_stride - 1) / a.k1_stride) * a.k1_stride : k1_begin;
+    const int k1_step = unit ? a.k1_stride : 1;
+    for (int k1 = any ? k1_first : k1_end; k1 < k1_end; k1 += k1_step) {
       const int g1[3] = {k1 / (a.grid[1] * a.grid[2]), (k1 / a.grid[2]) % a.grid[1], k1 % a.grid[2]};
       for (int o = tid; o < NB2; o += nthr) sE1[o] = ld_e<R>(a, (size_t)k1 * NB2 + o);
       for (int o = tid; o < NB; o += nthr) {
@@ -423,7 +427,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
       }
       __syncthreads();
       // Psi[jj][j1][grp][gt]
-      const int npsi = J * NB * G * 9;
+      const int npsi = unit ? 0 : J * NB * G * 9;
       for (int o = tid; o < npsi; o += nthr) {
         const int gt = o % 9;
         const int t9 = o / 9;
@@ -453,7 +457,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
       }
       __syncthreads();
 
-      for (int k2 = k1; k2 < N; ++k2) {
+      for (int k2 = unit ? 0 : k1; k2 < N; ++k2) {
         // ---- phase 1: per-k2 tables
         const int g2[3] = {k2 / (a.grid[1] * a.grid[2]), (k2 / a.grid[2]) % a.grid[1], k2 % a.grid[2]};
         const int g3[3] = {(g[0] + g1[0] + g2[0]) % a.grid[0], (g[1] + g1[1] + g2[1]) % a.grid[1],
@@ -517,7 +521,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
             sigma_f_from_exact(sSig + 2 * o, sSigPM + o, sSigI + o);
           }
         }
-        if (has_row) {
+        if (has_row && !unit) {
           // A row (jj, j1 = rj1, c = rc): d = (l, theta)
           C Arow[NB];
 #pragma unroll
@@ -552,7 +556,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
           const float h0 = sHq[rjj], l0 = sLq[rjj];
           const float hx = sH1[x], hy = sH2[y];
           // candidates 0..2: ordering A (q' = (k1,x), q'' = (k2,y)) ++, +-, --; 3..5: ordering B, swapped
-          const unsigned cand = (k1 != k2) ? 0x3Fu : 0x07u;
+          const unsigned cand = (k1 != k2 && !unit) ? 0x3Fu : 0x07u;
           if (hx != 0.f && hy != 0.f) {
             C e2row[NB];
 #pragma unroll
@@ -562,6 +566,24 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
             const float apy = ap + hy, apm = ap - hy, amm = am - hy;
             const float bpx = bp + hx, bpm = bp - hx, bmm = bm - hx;
             const float s0 = (h0 + hx) + hy;
+            // one temperature: the four distinct products c_p (1/(n0 w0)) x leg weights of this row, per
+            // candidate class (++ both orderings, +- ordering A, +- ordering B, -- both orderings)
+            R wpp = 0, wpa = 0, wpb = 0, wmm = 0;
+            if constexpr (MAXT == 1) {
+              if constexpr (kF64) {
+                const double f0 = sW0[rjj], a1 = sW1[2 * x], b1 = sW1[2 * x + 1], a2 = sW2[2 * y], b2 = sW2[2 * y + 1];
+                wpp = 0.5 * f0 * (a1 * a2);
+                wpa = 0.5 * f0 * (a1 * b2);
+                wpb = 0.5 * f0 * (a2 * b1);
+                wmm = (1.0 / 6.0) * f0 * (b1 * b2);
+              } else {
+                const float f0 = sF0[rjj], a1 = sF1[2 * x], b1 = sF1[2 * x + 1], a2 = sF2[2 * y], b2 = sF2[2 * y + 1];
+                wpp = 0.5f * f0 * (a1 * a2);
+                wpa = 0.5f * f0 * (a1 * b2);
+                wpb = 0.5f * f0 * (a2 * b1);
+                wmm = (1.0f / 6.0f) * f0 * (b1 * b2);
+              }
+            }
             const float2* PA0 = sSigPM + 0 * NB2 + y * NB;
             const float2* PA1 = sSigPM + 1 * NB2 + y * NB;
             const float2* PB0 = sSigPM + 2 * NB2 + x * NB;
@@ -580,12 +602,22 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
     accm |= (ad_ < (pm).x - M_ ? 1u : 0u) << (c);                        \
     band |= (ad_ <= (pm).x + M_ && !(ad_ < (pm).x - M_) ? 1u : 0u) << (c); \
   }
-              FP_SCREEN(0, apy - h3, a0)
+              // ++ in both orderings (and -- likewise) have nearly equal dw~ and are rarely accepted: one
+              // combined rejection (the same float comparisons as the individual tests) covers the pair
+              {
+                const float d0 = apy - h3, d3 = bpx - h3;
+                if (fminf(fabsf(d0), fabsf(d3)) <= fmaxf(a0.x + (sS + a0.y), b0.x + (sS + b0.y))) {
+                  FP_SCREEN(0, d0, a0)
+                  FP_SCREEN(3, d3, b0)
+                }
+                const float d2 = amm - h3, d5 = bmm - h3;
+                if (fminf(fabsf(d2), fabsf(d5)) <= fmaxf(a1.x + (sS + a1.y), b1.x + (sS + b1.y))) {
+                  FP_SCREEN(2, d2, a1)
+                  FP_SCREEN(5, d5, b1)
+                }
+              }
               FP_SCREEN(1, apm - h3, a1)
-              FP_SCREEN(2, amm - h3, a1)
-              FP_SCREEN(3, bpx - h3, b0)
               FP_SCREEN(4, bpm - h3, b1)
-              FP_SCREEN(5, bmm - h3, b1)
 #undef FP_SCREEN
               accm &= cand;
               band &= cand;
@@ -607,9 +639,11 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
                 if (fabs(d64) <= P64) accm |= 1u << c;
               }
               if (!accm) continue;
-              C Wv = cmk<R>(0, 0);
+              C Wv = cmk<R>(unit ? 1 : 0, 0);
+              if (!unit) {
 #pragma unroll
-              for (int c = 0; c < NB; ++c) cfma(Wv, e2row[c], tb[c * NB + j3]);
+                for (int c = 0; c < NB; ++c) cfma(Wv, e2row[c], tb[c * NB + j3]);
+              }
               while (accm) {
                 const int c = __ffs(accm) - 1;
                 accm &= accm - 1;
@@ -632,14 +666,19 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
                     const double xx = d64 * inv;
                     delta = exp(-xx * xx) * inv * kInvSqrtPi;
                   }
-                  const double base = (p == 2 ? (1.0 / 6.0) : 0.5) * W2 * delta;
-                  const double* wq1 = ordA ? sW1 : sW2;
-                  const double* wq2 = ordA ? sW2 : sW1;
+                  if constexpr (MAXT == 1) {
+                    const double wsel = (p == 0) ? wpp : (p == 2) ? wmm : ordA ? wpa : wpb;
+                    acc[0] += (W2 * delta) * wsel * sW3[j3];
+                  } else {
+                    const double base = (p == 2 ? (1.0 / 6.0) : 0.5) * W2 * delta;
+                    const double* wq1 = ordA ? sW1 : sW2;
+                    const double* wq2 = ordA ? sW2 : sW1;
 #pragma unroll
-                  for (int t = 0; t < MAXT; ++t) {
-                    if (t >= nT) break;
-                    acc[t] += base * sW0[t * J + rjj] * wq1[2 * (t * NB + i1) + s1] * wq2[2 * (t * NB + i2) + s2] *
-                              sW3[t * NB + j3];
+                    for (int t = 0; t < MAXT; ++t) {
+                      if (t >= nT) break;
+                      acc[t] += base * sW0[t * J + rjj] * wq1[2 * (t * NB + i1) + s1] *
+                                wq2[2 * (t * NB + i2) + s2] * sW3[t * NB + j3];
+                    }
                   }
                 } else {
                   const float W2 = Wv.re * Wv.re + Wv.im * Wv.im;
@@ -659,18 +698,27 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
                     const float xx = dwf * inv;
                     delta = __expf(-xx * xx) * inv * (float)kInvSqrtPi;
                   }
-                  const float base = ((p == 2) ? (1.0f / 6.0f) : 0.5f) * W2 * delta;
-                  const float* fq1 = ordA ? sF1 : sF2;
-                  const float* fq2 = ordA ? sF2 : sF1;
-#pragma unroll
-                  for (int t = 0; t < MAXT; ++t) {
-                    if (t >= nT) break;
-                    const float term = base * sF0[t * J + rjj] * fq1[2 * (t * NB + i1) + s1] *
-                                       fq2[2 * (t * NB + i2) + s2] * sF3[t * NB + j3];
+                  if constexpr (MAXT == 1) {
+                    const float wsel = (p == 0) ? wpp : (p == 2) ? wmm : ordA ? wpa : wpb;
+                    const float term = (W2 * delta) * wsel * sF3[j3];
                     float s, e;
-                    two_sum(acch[t], term, s, e);
-                    acch[t] = s;
-                    accl[t] += e;
+                    two_sum(acch[0], term, s, e);
+                    acch[0] = s;
+                    accl[0] += e;
+                  } else {
+                    const float base = ((p == 2) ? (1.0f / 6.0f) : 0.5f) * W2 * delta;
+                    const float* fq1 = ordA ? sF1 : sF2;
+                    const float* fq2 = ordA ? sF2 : sF1;
+#pragma unroll
+                    for (int t = 0; t < MAXT; ++t) {
+                      if (t >= nT) break;
+                      const float term = base * sF0[t * J + rjj] * fq1[2 * (t * NB + i1) + s1] *
+                                         fq2[2 * (t * NB + i2) + s2] * sF3[t * NB + j3];
+                      float s, e;
+                      two_sum(acch[t], term, s, e);
+                      acch[t] = s;
+                      accl[t] += e;
+                    }
                   }
                 }
               }

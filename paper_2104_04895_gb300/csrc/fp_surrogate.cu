@@ -120,11 +120,12 @@ __global__ void bose_kernel(const double* omega, int nm, int nT, const double* T
 
 // ------------------------------------------------------------------------------------------------
 // Features per (temperature, mode): [w/wmax, |v|/vmax, branch one-hot (nb), log(T/300), log n0,
-// log P3, log WP3, cos and sin of 2 pi g_a / N_a (a = 1..3)] -> F = nb + 12 columns; rows r = t * N*nb + m.
+// log P3, log WP3, cos and sin of 2 pi g_a / N_a (a = 1..3), log WP4 (sampled)] -> F = nb + 13 columns;
+// rows r = t * N*nb + m.
 __global__ void features_kernel(const double* omega, const double* vel, const double* nbose, const double* p3,
-                                const double* wp3, const double* T, int nm, int nb, int nT, int g0, int g1n, int g2n,
-                                double wmax, double vmax, float* X) {
-  const int F = nb + 12;
+                                const double* wp3, const double* wp4, const double* T, int nm, int nb, int nT,
+                                int g0, int g1n, int g2n, double wmax, double vmax, float* X) {
+  const int F = nb + 13;
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nm * nT) return;
   const int t = r / nm, m = r % nm;
@@ -147,6 +148,7 @@ __global__ void features_kernel(const double* omega, const double* vel, const do
     x[6 + nb + 2 * a] = (float)cv;
     x[7 + nb + 2 * a] = (float)sv;
   }
+  x[12 + nb] = (float)log(fabs(wp4[r]) + 1e-30);
 }
 
 // column mean and standard deviation over the listed rows (one thread per column, fixed order)
@@ -470,6 +472,31 @@ extern "C" int fp_phase3(fp_ctx* c, int nT, const double* T, double sb, const fp
   return FP_OK;
 }
 
+extern "C" int fp_phase4(fp_ctx* c, int nT, const double* T, double sb, int stride, double* wp4) {
+  using namespace fp;
+  if (!c) return FP_EINVAL;
+  if (!c->have_modes) return sfail(c, FP_ESTATE, "fp_phase4: call fp_modes or fp_set_modes first");
+  if (nT < 1 || nT > kMaxT || !T) return sfail(c, FP_EINVAL, "fp_phase4: nT must be in [1, 8]");
+  for (int i = 0; i < nT; ++i)
+    if (!(T[i] > 0.0)) return sfail(c, FP_EINVAL, "fp_phase4: temperatures must be > 0");
+  if (!(sb > 0.0) || stride < 1 || stride > c->N) return sfail(c, FP_EINVAL, "fp_phase4: bad scalebroad or stride");
+  if (!wp4) return sfail(c, FP_EINVAL, "fp_phase4: NULL output");
+  SG_CUDA(c, cudaSetDevice(c->device));
+  const size_t n = (size_t)nT * c->N * c->nb;
+  double* d = nullptr;
+  SG_CUDA(c, dalloc(&d, n));
+  std::string err;
+  int rc = phase4_sampled(c, nT, T, sb, stride, d, &err);
+  if (rc) {
+    cudaFree(d);
+    return sfail(c, rc, "fp_phase4: " + err);
+  }
+  cudaError_t e = cudaMemcpy(wp4, d, n * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return sfail(c, FP_ECUDA, std::string("fp_phase4: ") + cudaGetErrorString(e));
+  return FP_OK;
+}
+
 extern "C" int fp_mlp_loss_grad(int device, int n_in, int batch, const float* X, const float* y,
                                 const float* params, float* grad, float* loss) {
   using namespace fp;
@@ -533,7 +560,7 @@ extern "C" int fp_surrogate_fit(fp_ctx* c, int nT, const double* T, double sb, c
   const double t_start = now_ms();
   SG_CUDA(c, cudaSetDevice(c->device));
   cudaStream_t s = c->stream;
-  const int nb = c->nb, nm = c->N * nb, F = nb + 12;
+  const int nb = c->nb, nm = c->N * nb, F = nb + 13;
   const size_t rows_all = (size_t)nm * nT;
 
   // modes with positive frequency, shuffled with the seeded generator
@@ -567,7 +594,7 @@ extern "C" int fp_surrogate_fit(fp_ctx* c, int nT, const double* T, double sb, c
 
   // features for every (temperature, mode)
   t0 = now_ms();
-  double *dT = nullptr, *dn = nullptr, *dp3 = nullptr, *dwp3 = nullptr;
+  double *dT = nullptr, *dn = nullptr, *dp3 = nullptr, *dwp3 = nullptr, *dwp4 = nullptr;
   float *dX = nullptr, *dY = nullptr, *dmean = nullptr, *dstd = nullptr;
   int* drows = nullptr;
   std::vector<int> train_rows;
@@ -582,6 +609,7 @@ extern "C" int fp_surrogate_fit(fp_ctx* c, int nT, const double* T, double sb, c
     cudaFree(dn);
     cudaFree(dp3);
     cudaFree(dwp3);
+    cudaFree(dwp4);
     cudaFree(dX);
     cudaFree(dY);
     cudaFree(dmean);
@@ -603,6 +631,7 @@ extern "C" int fp_surrogate_fit(fp_ctx* c, int nT, const double* T, double sb, c
   SG_TRY(dalloc(&dn, rows_all));
   SG_TRY(dalloc(&dp3, (size_t)nm));
   SG_TRY(dalloc(&dwp3, rows_all));
+  SG_TRY(dalloc(&dwp4, rows_all));
   SG_TRY(dalloc(&dX, rows_all * F));
   SG_TRY(dalloc(&dY, rows_all));
   SG_TRY(dalloc(&dmean, F));
@@ -634,6 +663,16 @@ extern "C" int fp_surrogate_fit(fp_ctx* c, int nT, const double* T, double sb, c
     phase3_kernel<<<(unsigned)(((size_t)nm * 32 + 255) / 256), 256, 0, s>>>(a);
     SG_TRY(cudaGetLastError());
   }
+  {
+    // sampled four-phonon weighted phase space: q' on a stride giving about 1/16 of the ordered pairs
+    const int stride = std::max(1, c->N / 32);
+    std::string perr;
+    const int prc = phase4_sampled(c, nT, T, sb, stride, dwp4, &perr);
+    if (prc) {
+      cleanup();
+      return sfail(c, prc, "fp_surrogate_fit: " + perr);
+    }
+  }
   double wmax = 0.0;
   for (double w : om) wmax = std::max(wmax, w);
   std::vector<double> vel((size_t)nm * 3);
@@ -643,8 +682,8 @@ extern "C" int fp_surrogate_fit(fp_ctx* c, int nT, const double* T, double sb, c
   for (int m = 0; m < nm; ++m)
     vmax = std::max(vmax, std::sqrt(vel[3 * m] * vel[3 * m] + vel[3 * m + 1] * vel[3 * m + 1] +
                                     vel[3 * m + 2] * vel[3 * m + 2]));
-  features_kernel<<<(unsigned)((rows_all + 255) / 256), 256, 0, s>>>(c->d_omega, c->d_vel, dn, dp3, dwp3, dT, nm,
-                                                                     nb, nT, c->grid[0], c->grid[1], c->grid[2],
+  features_kernel<<<(unsigned)((rows_all + 255) / 256), 256, 0, s>>>(c->d_omega, c->d_vel, dn, dp3, dwp3, dwp4, dT,
+                                                                     nm, nb, nT, c->grid[0], c->grid[1], c->grid[2],
                                                                      wmax, vmax, dX);
   SG_TRY(cudaMemcpyAsync(drows, train_rows.data(), train_rows.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   col_stats_kernel<<<1, 64, 0, s>>>(dX, F, drows, (int)train_rows.size(), dmean, dstd);
@@ -719,7 +758,7 @@ extern "C" int fp_surrogate_fit(fp_ctx* c, int nT, const double* T, double sb, c
     return (m % nb) * 4 + qb;
   };
   const int nbins = nb * 4;
-  std::vector<double> bin_err(nbins, 0.0);
+  std::vector<double> bin_err(nbins, 0.0), bin_err2(nbins, 0.0);
   std::vector<int> bin_cnt(nbins, 0);
   std::vector<double> errs;
   for (int m = 0; m < nm; ++m) {
@@ -730,13 +769,21 @@ extern "C" int fp_surrogate_fit(fp_ctx* c, int nT, const double* T, double sb, c
       const double e = std::fabs(pred[r] - exact[r]) / exact[r];
       errs.push_back(e);
       bin_err[bin_of(m)] += e;
+      bin_err2[bin_of(m)] += e * e;
       bin_cnt[bin_of(m)] += 1;
     }
   }
   int n_bins_fb = 0;
   std::vector<unsigned char> bin_fb(nbins, 0);
+  // a bin stays on the network only when it has at least 16 held-out rows and the upper confidence bound
+  // (mean + 2 standard errors) of their relative error is within the tolerance
   for (int b = 0; b < nbins; ++b) {
-    const double e = bin_cnt[b] ? bin_err[b] / bin_cnt[b] : 1e30;
+    double e = 1e30;
+    if (bin_cnt[b] >= 16) {
+      const double n = bin_cnt[b], mu = bin_err[b] / n;
+      const double var = std::max(0.0, bin_err2[b] / n - mu * mu);
+      e = mu + 2.0 * std::sqrt(var / n);
+    }
     if (e > so.tol) {
       bin_fb[b] = 1;
       ++n_bins_fb;

@@ -86,3 +86,20 @@ def test_errors(lib):
         assert ei.value.code == FP_EINVAL
         out, _ = ctx.rates4([300.0])   # the context is still usable after rejected calls
         assert np.all(np.isfinite(out))
+
+
+def test_injected_allocation_failure_is_reported_and_recoverable(lib, monkeypatch):
+    """FP_FAULT_ALLOC=k makes the k-th device allocation report out-of-memory (host-side injection)."""
+    from paper_2104_04895_gb300.binding import FP_ENOMEM
+    cr = synth.simple_cubic((2, 2, 2))
+    for k in (1, 3, 7):
+        monkeypatch.setenv("FP_FAULT_ALLOC", str(k))
+        with pytest.raises(FourPhononError) as ei:
+            lib.Context.from_crystal(cr)
+        assert ei.value.code == FP_ENOMEM
+        monkeypatch.delenv("FP_FAULT_ALLOC")
+    with lib.Context.from_crystal(cr) as ctx:   # nothing leaked or left broken
+        w, e, v = oracle_modes(cr)
+        ctx.set_modes(w, e, v)
+        out, _ = ctx.rates4([300.0])
+        assert np.all(np.isfinite(out))
