@@ -81,7 +81,7 @@ const void* rates_kernel_ptr(int precision, int nb, int nT) {
 }
 
 size_t smem_bytes(int precision, int nb, int J, int G, int nquart, int nT, int threads) {
-  Carve c = make_carve(nb, J, G, nquart, nT, threads);
+  Carve c = make_carve(nb, J, G, nquart, nT, threads, precision != FP_PREC_FP64);
   return c.bytes(precision == FP_PREC_FP64 ? sizeof(Cx<double>) : sizeof(Cx<float>));
 }
 

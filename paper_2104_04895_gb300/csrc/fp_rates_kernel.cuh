@@ -118,19 +118,45 @@ constexpr float kRelS = 1.0f / 524288.0f;         // 2^-19: prefilter margin per
 constexpr float kRelP = 1.0f / 4194304.0f;        // 2^-22: prefilter margin per unit of window*sigma
 constexpr float kAbsV = 1.0f / 1099511627776.0f;  // 2^-40: two-float velocity difference error per |v|_1
 
+// exp(-u) for the FP64 Gaussian, table-driven (P. T. P. Tang, ACM TOMS 15 (1989) 144-157): u = k h + r with
+// h = 1/32 and |r| <= h/2, exp(-u) = exp(-k h) exp(-r); exp(-k h) comes from a table of kExpTab entries
+// (0 <= u <= 4), exp(-r) from its Taylor polynomial of degree 6, whose truncation error (h/2)^7/7! < 5e-17 is
+// below half an ulp. Larger u (only when the window exceeds 2) takes exp().
+constexpr int kExpTab = 136;
+constexpr double kExpH = 1.0 / 32.0;
+__device__ __forceinline__ double exp_neg(double u, const double* tab) {
+  if (!(u <= 4.0)) return exp(-u);
+  const int k = __double2int_rn(u * 32.0);
+  const double s = fma((double)k, kExpH, -u);  // -r, exact
+  double p = 1.0 / 720.0;
+  p = fma(p, s, 1.0 / 120.0);
+  p = fma(p, s, 1.0 / 24.0);
+  p = fma(p, s, 1.0 / 6.0);
+  p = fma(p, s, 0.5);
+  p = fma(p, s, 1.0);
+  p = fma(p, s, 1.0);
+  return tab[k] * p;
+}
+
 // Shared-memory carve shared by the kernel and the host-side size query.
 struct Carve {
-  size_t E0, E1, E2, E3, Psi, T, Tw2, TwQ, ncx;                               // complex elements
-  size_t Om0, Om1, Om2, Om3, V1, V2, V3, Sig, W0, W1, W2, W3, Red, ndbl;       // doubles
+  size_t E0, E1, E2, E3, Psi, T, Tw2, TwQ, QW, ncx;                           // complex elements
+  size_t Om0, Om1, Om2, Om3, V1, V2, V3, Sig, W0, W1, W2, W3, Red, Wp, ndbl, ExpT;  // doubles
   size_t Hq, Lq, H1, L1, H2, L2, H3, L3, VH1, VL1, VH2, VL2, VH3, VL3, Sigf, F0, F1, F2, F3, nflt;  // floats
-  size_t KL, nint;                                                            // ints
+  size_t KL, QI, nint;                                                        // ints
   size_t Mask;                                                                // bytes
   size_t bytes(size_t cx_size) const {
     return ncx * cx_size + ndbl * sizeof(double) + nflt * sizeof(float) + nint * sizeof(int) + Mask + 16;
   }
 };
 
-__host__ __device__ inline Carve make_carve(int nb, int J, int G, int nquart, int nT, int threads) {
+// terms queued per warp in the screening phase (a power of two)
+constexpr int kQCap = 128;
+// accumulator slots per lane: the j0 values that the 32 rows of one warp can span
+__host__ __device__ constexpr int acc_slots(int nb) { return nb == 3 ? 3 : 2; }
+
+// f32: the FP32 path, which has no term queue, weight-product rows or exp table
+__host__ __device__ inline Carve make_carve(int nb, int J, int G, int nquart, int nT, int threads, bool f32) {
   Carve c;
   const size_t nb2 = (size_t)nb * nb, nb3 = nb2 * nb, na = nb / 3;
   const size_t rows = (size_t)J * nb2;
@@ -143,6 +169,8 @@ __host__ __device__ inline Carve make_carve(int nb, int J, int G, int nquart, in
   c.T = o; o += (size_t)J * nb * (nb2 + 1);  // (j0, j1) blocks padded by one entry (bank spread)
   c.Tw2 = o; o += G;
   c.TwQ = o; o += nquart;
+  const size_t nwarps = ((size_t)threads + 31) / 32;
+  c.QW = o; o += f32 ? 0 : nwarps * kQCap;  // FP64: queued vertices
   c.ncx = o;
   size_t d = 0;
   c.Om0 = d; d += J;
@@ -157,7 +185,9 @@ __host__ __device__ inline Carve make_carve(int nb, int J, int G, int nquart, in
   c.W1 = d; d += 2 * (size_t)nT * nb;
   c.W2 = d; d += 2 * (size_t)nT * nb;
   c.W3 = d; d += (size_t)nT * nb;
-  c.Red = d; d += rows * nT;
+  c.Red = d; d += (size_t)threads * acc_slots(nb) * nT;
+  c.Wp = d; d += f32 ? 0 : (size_t)threads * 4;  // FP64, one temperature: per-row weight products
+  c.ExpT = d; d += f32 ? 0 : kExpTab;
   c.ndbl = d;
   size_t f = 0;
   c.Hq = f; f += J;
@@ -182,9 +212,9 @@ __host__ __device__ inline Carve make_carve(int nb, int J, int G, int nquart, in
   c.nflt = f;
   size_t k = 0;
   c.KL = k; k += na * na + 1 + G;
+  c.QI = k; k += f32 ? 0 : nwarps * kQCap;  // FP64: queued term indices
   c.nint = k;
   c.Mask = (size_t)J;
-  (void)threads;
   return c;
 }
 
@@ -274,6 +304,53 @@ __host__ __device__ constexpr int max_threads_for(int nb) { return nb == 3 ? 128
 template <typename R>
 __host__ __device__ constexpr int min_blocks_for() { return sizeof(R) == 4 ? FP_F32_MIN_BLOCKS : 2; }
 
+// Window test of the six candidates of entry (x, y, j3), written as a macro over the names of the
+// screening scope (row sums apy .. bmm, h3, sS, the sigma pairs a0 a1 b0 b1, cand, w0): sets accm to the
+// accepted candidates. The FP32 prefilter accepts when |dw~| < P - M and rejects when |dw~| > P + M;
+// candidates in between (band) are decided in FP64 exactly as the FP64 definition decides them.
+#define FP_SCREEN(c, dv, pm)                                               \
+  {                                                                        \
+    const float M_ = sS + (pm).y, ad_ = fabsf(dv);                         \
+    accm |= (ad_ < (pm).x - M_ ? 1u : 0u) << (c);                          \
+    band |= (ad_ <= (pm).x + M_ && !(ad_ < (pm).x - M_) ? 1u : 0u) << (c); \
+  }
+// ++ in both orderings (and -- likewise) have nearly equal dw~ and are rarely accepted: one combined
+// rejection (the same float comparisons as the individual tests) covers the pair
+#define FP_WINDOW_TEST()                                                                               \
+  {                                                                                                    \
+    const float d0 = apy - h3, d3 = bpx - h3;                                                          \
+    if (fminf(fabsf(d0), fabsf(d3)) <= fmaxf(a0.x + (sS + a0.y), b0.x + (sS + b0.y))) {                \
+      FP_SCREEN(0, d0, a0)                                                                             \
+      FP_SCREEN(3, d3, b0)                                                                             \
+    }                                                                                                  \
+    const float d2 = amm - h3, d5 = bmm - h3;                                                          \
+    if (fminf(fabsf(d2), fabsf(d5)) <= fmaxf(a1.x + (sS + a1.y), b1.x + (sS + b1.y))) {                \
+      FP_SCREEN(2, d2, a1)                                                                             \
+      FP_SCREEN(5, d5, b1)                                                                             \
+    }                                                                                                  \
+    FP_SCREEN(1, apm - h3, a1)                                                                         \
+    FP_SCREEN(4, bpm - h3, b1)                                                                         \
+    accm &= cand;                                                                                      \
+    band &= cand;                                                                                      \
+    while (band) {                                                                                     \
+      const int c_ = __ffs(band) - 1;                                                                  \
+      band &= band - 1;                                                                                \
+      const int tab_ = (c_ < 3) ? (c_ == 0 ? 0 : 1) : (c_ == 3 ? 2 : 3);                              \
+      const int ent_ = tab_ * NB2 + ((c_ < 3) ? y : x) * NB + j3;                                      \
+      const double d64_ = dw_fp64(c_, w0, sOm1[x], sOm2[y], sOm3[j3]);                                 \
+      double P64_;                                                                                     \
+      if (kF64 || !f32_sigma) {                                                                        \
+        P64_ = sSig[2 * ent_];                                                                         \
+      } else {                                                                                         \
+        double ex_[2];                                                                                 \
+        const double* vl_ = ((tab_ < 2) ? sV2 + 3 * y : sV1 + 3 * x);                                  \
+        sigma_entry(a, vl_, (tab_ & 1) ? -1.0 : 1.0, sV3 + 3 * j3, ex_);                               \
+        P64_ = ex_[0];                                                                                 \
+      }                                                                                                \
+      if (fabs(d64_) <= P64_) accm |= 1u << c_;                                                        \
+    }                                                                                                  \
+  }
+
 template <typename R, int NB, int MAXT>
 __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rates_kernel(RatesArgs a) {
   constexpr int NB2 = NB * NB, NB3 = NB2 * NB, NA = NB / 3;
@@ -284,7 +361,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
   const int J = a.J, G = a.G, nT = a.nT, N = a.N;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int rows = J * NB2;
-  const Carve cv = make_carve(NB, J, G, a.nquart, nT, nthr);
+  const Carve cv = make_carve(NB, J, G, a.nquart, nT, nthr, !kF64);
   C* cx = reinterpret_cast<C*>(smem);
   C* sE0 = cx + cv.E0;
   C* sE1 = cx + cv.E1;
@@ -294,6 +371,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
   C* sT = cx + cv.T;
   C* sTw2 = cx + cv.Tw2;
   C* sTwQ = cx + cv.TwQ;
+  C* sQW = cx + cv.QW;  // [warp][kQCap]
   double* db = reinterpret_cast<double*>(cx + cv.ncx);
   double* sOm0 = db + cv.Om0;
   double* sOm1 = db + cv.Om1;
@@ -308,6 +386,8 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
   double* sW2 = db + cv.W2;
   double* sW3 = db + cv.W3;
   double* sRed = db + cv.Red;
+  double* sExpT = db + cv.ExpT;
+  double* sWp = db + cv.Wp;  // [thread][4] (FP64, one temperature)
   float* fb = reinterpret_cast<float*>(db + cv.ndbl);
   float* sHq = fb + cv.Hq;
   float* sLq = fb + cv.Lq;
@@ -332,6 +412,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
   int* ib = reinterpret_cast<int*>(fb + cv.nflt);
   int* sKLs = ib + cv.KL;            // [NA*NA + 1]
   int* sKLg = sKLs + NA * NA + 1;    // [G]
+  int* sQI = ib + cv.QI;             // [warp][kQCap]
   unsigned char* sMask = reinterpret_cast<unsigned char*>(ib + cv.nint);
 
   // the row this thread owns in the contraction and screening phases
@@ -340,7 +421,13 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
   const size_t NM = (size_t)N * NB;
   const bool f32_sigma = !kF64 && a.dq_mode == 0;
   unsigned long long cnt0 = 0, cnt1 = 0, cnt2 = 0;
+  constexpr int S = acc_slots(NB);
+  const int lane = tid & 31;
+  const int qbase = (tid >> 5) * kQCap;
+  const int jj_lo = (tid & ~31) / NB2;  // the j0 of this warp's first row; its rows span jj_lo .. jj_lo + S - 1
 
+  if constexpr (kF64)
+    for (int o = tid; o < kExpTab; o += nthr) sExpT[o] = exp(-(double)o * kExpH);
   for (int o = tid; o < NA * NA + 1; o += nthr) sKLs[o] = a.kl_start[o];
   for (int o = tid; o < G; o += nthr) sKLg[o] = a.kl_grp[o];
 
@@ -379,14 +466,58 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
     for (int jj = 0; jj < J; ++jj) any |= sMask[jj];
     const bool active = has_row && sMask[rjj];
 
-    double acc[MAXT];
-    float acch[MAXT], accl[MAXT];
+    double acc[S][MAXT];
+    float acch[S][MAXT], accl[S][MAXT];
 #pragma unroll
-    for (int t = 0; t < MAXT; ++t) {
-      acc[t] = 0.0;
-      acch[t] = 0.f;
-      accl[t] = 0.f;
-    }
+    for (int sl = 0; sl < S; ++sl)
+#pragma unroll
+      for (int t = 0; t < MAXT; ++t) {
+        acc[sl][t] = 0.0;
+        acch[sl][t] = 0.f;
+        accl[sl][t] = 0.f;
+      }
+    // FP64 path: one queued term (vertex Wv; info = c | j3 << 3 | y << 7 | x << 11 | jj << 15): Gaussian,
+    // Bose weights and |W|^2 into the accumulator slot of its j0
+    auto consume = [&](const C Wv, const int info) {
+      const int c = info & 7, j3 = (info >> 3) & 15, iy = (info >> 7) & 15, ix = (info >> 11) & 15;
+      const int jq = info >> 15;
+      const int slot = jq - jj_lo;
+      const int p = c % 3;
+      const bool ordA = c < 3;
+      const int tab = ordA ? (c == 0 ? 0 : 1) : (c == 3 ? 2 : 3);
+      const int ent = tab * NB2 + (ordA ? iy : ix) * NB + j3;
+      // Bose selectors: leg q' takes (1+n)/w unless --, leg q'' takes (1+n)/w only for ++
+      const int s1 = (p == 2) ? 1 : 0, s2 = (p == 0) ? 0 : 1;
+      const int i1 = ordA ? ix : iy, i2 = ordA ? iy : ix;
+      const int cls = (p == 0) ? 0 : (p == 2) ? 3 : ordA ? 1 : 2;
+      const double W2 = Wv.re * Wv.re + Wv.im * Wv.im;
+      const double d64 = dw_fp64(c, sOm0[jq], sOm1[ix], sOm2[iy], sOm3[j3]);
+      const double inv = sSig[2 * ent + 1];
+      double delta = 1.0;
+      if (inv >= 0.0) {
+        const double xx = d64 * inv;
+        delta = exp_neg(xx * xx, sExpT) * inv * kInvSqrtPi;
+      }
+      if constexpr (MAXT == 1) {
+        const double term = (W2 * delta) * sWp[4 * (jq * NB2 + ix * NB + iy) + cls] * sW3[j3];
+#pragma unroll
+        for (int sl = 0; sl < S; ++sl)
+          if (sl == slot) acc[sl][0] += term;
+      } else {
+        const double base = (p == 2 ? (1.0 / 6.0) : 0.5) * W2 * delta;
+        const double* wq1 = ordA ? sW1 : sW2;
+        const double* wq2 = ordA ? sW2 : sW1;
+#pragma unroll
+        for (int t = 0; t < MAXT; ++t) {
+          if (t >= nT) break;
+          const double term = base * sW0[t * J + jq] * wq1[2 * (t * NB + i1) + s1] *
+                              wq2[2 * (t * NB + i2) + s2] * sW3[t * NB + j3];
+#pragma unroll
+          for (int sl = 0; sl < S; ++sl)
+            if (sl == slot) acc[sl][t] += term;
+        }
+      }
+    };
 
     const int k1_begin = tile * a.t1;
     const int k1_end = min(N, k1_begin + a.t1);
@@ -549,7 +680,104 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
           }
         }
         __syncthreads();
-        // ---- phase 3: W row (jj, x, y) in registers, then window, Gaussian and Bose weights
+        if constexpr (kF64) {
+        // ---- phase 3 (FP64 path): every lane screens the window of its row (jj, x, y) for all j3; the accepted
+        // (entry, candidate) terms enter a per-warp queue and the warp evaluates them 32 at a time, so the
+        // Gaussian and Bose arithmetic runs on full warps however unevenly the accepted terms fall on lanes
+        {
+          const int x = rj1, y = rc;
+          const int jq0 = active ? rjj : 0;
+          const bool row_ok = active && sH1[x] != 0.f && sH2[y] != 0.f;
+          // candidates 0..2: ordering A (q' = (k1,x), q'' = (k2,y)) ++, +-, --; 3..5: ordering B, swapped
+          const unsigned cand = (k1 != k2 && !unit) ? 0x3Fu : 0x07u;
+          const double w0 = sOm0[jq0];
+          const float h0 = sHq[jq0];
+          const float hx = sH1[x], hy = sH2[y];
+          const float ap = h0 + hx, am = h0 - hx, bp = h0 + hy, bm = h0 - hy;
+          const float apy = ap + hy, apm = ap - hy, amm = am - hy;
+          const float bpx = bp + hx, bpm = bp - hx, bmm = bm - hx;
+          const float s0 = (h0 + hx) + hy;
+          C e2row[NB];
+#pragma unroll
+          for (int c = 0; c < NB; ++c) e2row[c] = sE2[y * NB + c];
+          const C* tb = sT + (size_t)(jq0 * NB + x) * (NB2 + 1);
+          if constexpr (MAXT == 1) {
+            // the four distinct products c_p (1/(n0 w0)) x leg weights of this row, per candidate class
+            // (++ both orderings, +- ordering A, +- ordering B, -- both orderings), read by any lane
+            if (row_ok) {
+              const double f0 = sW0[jq0], a1 = sW1[2 * x], b1 = sW1[2 * x + 1], a2 = sW2[2 * y], b2 = sW2[2 * y + 1];
+              double* wp = sWp + 4 * tid;
+              wp[0] = 0.5 * f0 * (a1 * a2);
+              wp[1] = 0.5 * f0 * (a1 * b2);
+              wp[2] = 0.5 * f0 * (a2 * b1);
+              wp[3] = (1.0 / 6.0) * f0 * (b1 * b2);
+            }
+          }
+          const float2* PA0 = sSigPM + 0 * NB2 + y * NB;
+          const float2* PA1 = sSigPM + 1 * NB2 + y * NB;
+          const float2* PB0 = sSigPM + 2 * NB2 + x * NB;
+          const float2* PB1 = sSigPM + 3 * NB2 + x * NB;
+          int qh = 0, qn = 0;  // warp-uniform queue head and length
+#pragma unroll 1
+          for (int j3 = 0; j3 < NB; ++j3) {
+            const float h3 = sH3[j3];
+            if (h3 == 0.f) continue;  // uniform: j3 and k2 are the same on all lanes
+            unsigned accm = 0;
+            C Wv = cmk<R>(unit ? 1 : 0, 0);
+            if (row_ok) {
+              const float sS = kRelS * (s0 + h3);
+              const float2 a0 = PA0[j3], a1 = PA1[j3], b0 = PB0[j3], b1 = PB1[j3];
+              unsigned band = 0;
+              FP_WINDOW_TEST()
+              if (accm && !unit) {
+#pragma unroll
+                for (int c = 0; c < NB; ++c) cfma(Wv, e2row[c], tb[c * NB + j3]);
+              }
+              cnt0 += __popc(accm & 0x09u);
+              cnt1 += __popc(accm & 0x12u);
+              cnt2 += __popc(accm & 0x24u);
+            }
+            // enqueue: lane offsets by an inclusive scan of the per-lane counts
+            const int nmy = __popc(accm);
+            int incl = nmy;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const int v = __shfl_up_sync(0xffffffffu, incl, o);
+              if (lane >= o) incl += v;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            int pos = qn + incl - nmy;
+            const int info0 = (j3 << 3) | (y << 7) | (x << 11) | (jq0 << 15);
+            while (accm) {
+              const int c = __ffs(accm) - 1;
+              accm &= accm - 1;
+              if (pos < kQCap) {
+                const int sl = (qh + pos) & (kQCap - 1);
+                sQW[qbase + sl] = Wv;
+                sQI[qbase + sl] = info0 | c;
+              } else {
+                consume(Wv, info0 | c);  // queue full (rare): the producing lane evaluates the term
+              }
+              ++pos;
+            }
+            qn = min(qn + total, kQCap);
+            __syncwarp();
+            while (qn >= 32) {
+              const int sl = (qh + lane) & (kQCap - 1);
+              consume(sQW[qbase + sl], sQI[qbase + sl]);
+              qh = (qh + 32) & (kQCap - 1);
+              qn -= 32;
+            }
+            __syncwarp();
+          }
+          if (lane < qn) {
+            const int sl = (qh + lane) & (kQCap - 1);
+            consume(sQW[qbase + sl], sQI[qbase + sl]);
+          }
+          __syncwarp();
+        }
+        } else {
+        // ---- phase 3 (FP32 path): W row (jj, x, y) in registers, then window, Gaussian and Bose weights
         if (active) {
           const int x = rj1, y = rc;
           const double w0 = sOm0[rjj];
@@ -568,21 +796,13 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
             const float s0 = (h0 + hx) + hy;
             // one temperature: the four distinct products c_p (1/(n0 w0)) x leg weights of this row, per
             // candidate class (++ both orderings, +- ordering A, +- ordering B, -- both orderings)
-            R wpp = 0, wpa = 0, wpb = 0, wmm = 0;
+            float wpp = 0.f, wpa = 0.f, wpb = 0.f, wmm = 0.f;
             if constexpr (MAXT == 1) {
-              if constexpr (kF64) {
-                const double f0 = sW0[rjj], a1 = sW1[2 * x], b1 = sW1[2 * x + 1], a2 = sW2[2 * y], b2 = sW2[2 * y + 1];
-                wpp = 0.5 * f0 * (a1 * a2);
-                wpa = 0.5 * f0 * (a1 * b2);
-                wpb = 0.5 * f0 * (a2 * b1);
-                wmm = (1.0 / 6.0) * f0 * (b1 * b2);
-              } else {
-                const float f0 = sF0[rjj], a1 = sF1[2 * x], b1 = sF1[2 * x + 1], a2 = sF2[2 * y], b2 = sF2[2 * y + 1];
-                wpp = 0.5f * f0 * (a1 * a2);
-                wpa = 0.5f * f0 * (a1 * b2);
-                wpb = 0.5f * f0 * (a2 * b1);
-                wmm = (1.0f / 6.0f) * f0 * (b1 * b2);
-              }
+              const float f0 = sF0[rjj], a1 = sF1[2 * x], b1 = sF1[2 * x + 1], a2 = sF2[2 * y], b2 = sF2[2 * y + 1];
+              wpp = 0.5f * f0 * (a1 * a2);
+              wpa = 0.5f * f0 * (a1 * b2);
+              wpb = 0.5f * f0 * (a2 * b1);
+              wmm = (1.0f / 6.0f) * f0 * (b1 * b2);
             }
             const float2* PA0 = sSigPM + 0 * NB2 + y * NB;
             const float2* PA1 = sSigPM + 1 * NB2 + y * NB;
@@ -595,55 +815,14 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
               const float sS = kRelS * (s0 + h3);
               const float2 a0 = PA0[j3], a1 = PA1[j3], b0 = PB0[j3], b1 = PB1[j3];
               unsigned accm = 0, band = 0;
-              // accept when |dw~| < P - M, reject when |dw~| > P + M, else decide in FP64
-#define FP_SCREEN(c, dv, pm)                                             \
-  {                                                                      \
-    const float M_ = sS + (pm).y, ad_ = fabsf(dv);                       \
-    accm |= (ad_ < (pm).x - M_ ? 1u : 0u) << (c);                        \
-    band |= (ad_ <= (pm).x + M_ && !(ad_ < (pm).x - M_) ? 1u : 0u) << (c); \
-  }
-              // ++ in both orderings (and -- likewise) have nearly equal dw~ and are rarely accepted: one
-              // combined rejection (the same float comparisons as the individual tests) covers the pair
-              {
-                const float d0 = apy - h3, d3 = bpx - h3;
-                if (fminf(fabsf(d0), fabsf(d3)) <= fmaxf(a0.x + (sS + a0.y), b0.x + (sS + b0.y))) {
-                  FP_SCREEN(0, d0, a0)
-                  FP_SCREEN(3, d3, b0)
-                }
-                const float d2 = amm - h3, d5 = bmm - h3;
-                if (fminf(fabsf(d2), fabsf(d5)) <= fmaxf(a1.x + (sS + a1.y), b1.x + (sS + b1.y))) {
-                  FP_SCREEN(2, d2, a1)
-                  FP_SCREEN(5, d5, b1)
-                }
-              }
-              FP_SCREEN(1, apm - h3, a1)
-              FP_SCREEN(4, bpm - h3, b1)
-#undef FP_SCREEN
-              accm &= cand;
-              band &= cand;
-              while (band) {
-                const int c = __ffs(band) - 1;
-                band &= band - 1;
-                const int tab = (c < 3) ? (c == 0 ? 0 : 1) : (c == 3 ? 2 : 3);
-                const int ent = tab * NB2 + ((c < 3) ? y : x) * NB + j3;
-                const double d64 = dw_fp64(c, w0, sOm1[x], sOm2[y], sOm3[j3]);
-                double P64;
-                if (kF64 || !f32_sigma) {
-                  P64 = sSig[2 * ent];
-                } else {
-                  double ex[2];
-                  const double* vl = ((tab < 2) ? sV2 + 3 * y : sV1 + 3 * x);
-                  sigma_entry(a, vl, (tab & 1) ? -1.0 : 1.0, sV3 + 3 * j3, ex);
-                  P64 = ex[0];
-                }
-                if (fabs(d64) <= P64) accm |= 1u << c;
-              }
+              FP_WINDOW_TEST()
               if (!accm) continue;
               C Wv = cmk<R>(unit ? 1 : 0, 0);
               if (!unit) {
 #pragma unroll
                 for (int c = 0; c < NB; ++c) cfma(Wv, e2row[c], tb[c * NB + j3]);
               }
+              const float W2 = Wv.re * Wv.re + Wv.im * Wv.im;
               while (accm) {
                 const int c = __ffs(accm) - 1;
                 accm &= accm - 1;
@@ -657,91 +836,82 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
                 // Bose selectors: leg q' takes (1+n)/w unless --, leg q'' takes (1+n)/w only for ++
                 const int s1 = (p == 2) ? 1 : 0, s2 = (p == 0) ? 0 : 1;
                 const int i1 = ordA ? x : y, i2 = ordA ? y : x;
-                if constexpr (kF64) {
-                  const double W2 = Wv.re * Wv.re + Wv.im * Wv.im;
-                  const double d64 = dw_fp64(c, w0, sOm1[x], sOm2[y], sOm3[j3]);
-                  const double inv = sSig[2 * ent + 1];
-                  double delta = 1.0;
-                  if (inv >= 0.0) {
-                    const double xx = d64 * inv;
-                    delta = exp(-xx * xx) * inv * kInvSqrtPi;
-                  }
-                  if constexpr (MAXT == 1) {
-                    const double wsel = (p == 0) ? wpp : (p == 2) ? wmm : ordA ? wpa : wpb;
-                    acc[0] += (W2 * delta) * wsel * sW3[j3];
-                  } else {
-                    const double base = (p == 2 ? (1.0 / 6.0) : 0.5) * W2 * delta;
-                    const double* wq1 = ordA ? sW1 : sW2;
-                    const double* wq2 = ordA ? sW2 : sW1;
-#pragma unroll
-                    for (int t = 0; t < MAXT; ++t) {
-                      if (t >= nT) break;
-                      acc[t] += base * sW0[t * J + rjj] * wq1[2 * (t * NB + i1) + s1] *
-                                wq2[2 * (t * NB + i2) + s2] * sW3[t * NB + j3];
-                    }
-                  }
+                // dw from two-float frequencies with error-free sums
+                const float fh = ordA ? hx : hy, fl = ordA ? sL1[x] : sL2[y];
+                const float sh = ordA ? hy : hx, sl = ordA ? sL2[y] : sL1[x];
+                const float sg1 = (p == 2) ? -1.f : 1.f, sg2 = (p == 0) ? 1.f : -1.f;
+                float t0, e1, e2, e3;
+                two_sum(h0, sg1 * fh, t0, e1);
+                two_sum(t0, sg2 * sh, t0, e2);
+                two_sum(t0, -h3, t0, e3);
+                const float lo = (((l0 + sg1 * fl) + sg2 * sl) - sL3[j3]) + ((e1 + e2) + e3);
+                const float dwf = t0 + lo;
+                const float inv = sSigI[ent];
+                float delta = 1.0f;
+                if (inv >= 0.f) {
+                  const float xx = dwf * inv;
+                  delta = __expf(-xx * xx) * inv * (float)kInvSqrtPi;
+                }
+                if constexpr (MAXT == 1) {
+                  const float wsel = (p == 0) ? wpp : (p == 2) ? wmm : ordA ? wpa : wpb;
+                  const float term = (W2 * delta) * wsel * sF3[j3];
+                  float s, e;
+                  two_sum(acch[0][0], term, s, e);
+                  acch[0][0] = s;
+                  accl[0][0] += e;
                 } else {
-                  const float W2 = Wv.re * Wv.re + Wv.im * Wv.im;
-                  // dw from two-float frequencies with error-free sums
-                  const float fh = ordA ? hx : hy, fl = ordA ? sL1[x] : sL2[y];
-                  const float sh = ordA ? hy : hx, sl = ordA ? sL2[y] : sL1[x];
-                  const float sg1 = (p == 2) ? -1.f : 1.f, sg2 = (p == 0) ? 1.f : -1.f;
-                  float t0, e1, e2, e3;
-                  two_sum(h0, sg1 * fh, t0, e1);
-                  two_sum(t0, sg2 * sh, t0, e2);
-                  two_sum(t0, -h3, t0, e3);
-                  const float lo = (((l0 + sg1 * fl) + sg2 * sl) - sL3[j3]) + ((e1 + e2) + e3);
-                  const float dwf = t0 + lo;
-                  const float inv = sSigI[ent];
-                  float delta = 1.0f;
-                  if (inv >= 0.f) {
-                    const float xx = dwf * inv;
-                    delta = __expf(-xx * xx) * inv * (float)kInvSqrtPi;
-                  }
-                  if constexpr (MAXT == 1) {
-                    const float wsel = (p == 0) ? wpp : (p == 2) ? wmm : ordA ? wpa : wpb;
-                    const float term = (W2 * delta) * wsel * sF3[j3];
-                    float s, e;
-                    two_sum(acch[0], term, s, e);
-                    acch[0] = s;
-                    accl[0] += e;
-                  } else {
-                    const float base = ((p == 2) ? (1.0f / 6.0f) : 0.5f) * W2 * delta;
-                    const float* fq1 = ordA ? sF1 : sF2;
-                    const float* fq2 = ordA ? sF2 : sF1;
+                  const float base = ((p == 2) ? (1.0f / 6.0f) : 0.5f) * W2 * delta;
+                  const float* fq1 = ordA ? sF1 : sF2;
+                  const float* fq2 = ordA ? sF2 : sF1;
 #pragma unroll
-                    for (int t = 0; t < MAXT; ++t) {
-                      if (t >= nT) break;
-                      const float term = base * sF0[t * J + rjj] * fq1[2 * (t * NB + i1) + s1] *
-                                         fq2[2 * (t * NB + i2) + s2] * sF3[t * NB + j3];
-                      float s, e;
-                      two_sum(acch[t], term, s, e);
-                      acch[t] = s;
-                      accl[t] += e;
-                    }
+                  for (int t = 0; t < MAXT; ++t) {
+                    if (t >= nT) break;
+                    const float term = base * sF0[t * J + rjj] * fq1[2 * (t * NB + i1) + s1] *
+                                       fq2[2 * (t * NB + i2) + s2] * sF3[t * NB + j3];
+                    float s, e;
+                    two_sum(acch[0][t], term, s, e);
+                    acch[0][t] = s;
+                    accl[0][t] += e;
                   }
                 }
               }
             }
           }
         }
+        }
         __syncthreads();
       }
     }
-    // deterministic reduction: per-row sums in shared memory, then rows of each j0 in order
-    if (has_row) {
+    // deterministic reduction. FP64: per-lane slot sums in shared memory, then for each j0 the lanes of the
+    // warps that hold its rows, in lane order. FP32: per-row sums, then the rows of each j0 in order.
+    if constexpr (kF64) {
+#pragma unroll
+      for (int sl = 0; sl < S; ++sl)
+#pragma unroll
+        for (int t = 0; t < MAXT; ++t) {
+          if (t >= nT) break;
+          sRed[((size_t)tid * S + sl) * nT + t] = acc[sl][t];
+        }
+    } else if (has_row) {
 #pragma unroll
       for (int t = 0; t < MAXT; ++t) {
         if (t >= nT) break;
-        sRed[(size_t)tid * nT + t] = kF64 ? acc[t] : (double)acch[t] + (double)accl[t];
+        sRed[(size_t)tid * nT + t] = (double)acch[0][t] + (double)accl[0][t];
       }
     }
     __syncthreads();
     for (int o = tid; o < J * nT; o += nthr) {
       const int jj = o / nT, t = o % nT;
-      double s = 0.0;
-      for (int r = 0; r < NB2; ++r) s += sRed[(size_t)(jj * NB2 + r) * nT + t];
-      a.partial[(size_t)item * J * nT + o] = s;
+      double sum = 0.0;
+      if constexpr (kF64) {
+        for (int w = (jj * NB2) >> 5; w <= ((jj + 1) * NB2 - 1) >> 5; ++w) {
+          const int sl = jj - (w * 32) / NB2;
+          for (int l = 0; l < 32 && w * 32 + l < nthr; ++l) sum += sRed[((size_t)(w * 32 + l) * S + sl) * nT + t];
+        }
+      } else {
+        for (int r = 0; r < NB2; ++r) sum += sRed[(size_t)(jj * NB2 + r) * nT + t];
+      }
+      a.partial[(size_t)item * J * nT + o] = sum;
     }
     __syncthreads();
   }
