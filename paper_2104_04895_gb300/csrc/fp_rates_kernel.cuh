@@ -551,48 +551,73 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
       }
       for (int Q = tid; Q < a.nquart; Q += nthr) {
         const int* m = a.qmeta + 9 * Q;
-        long long e = 0;
-        for (int d = 0; d < 3; ++d)
-          e += (long long)a.Lfac[d] * wrapi(g1[d] * m[3 + d] - (g[d] + g1[d]) * m[6 + d], a.grid[d]);
-        sTwQ[Q] = ld_tw<R>(a, (int)(e % a.L));
+        int e = 0;  // each term is below L, so e < 3 L
+        for (int d = 0; d < 3; ++d) e += a.Lfac[d] * wrapi(g1[d] * m[3 + d] - (g[d] + g1[d]) * m[6 + d], a.grid[d]);
+        while (e >= a.L) e -= a.L;
+        sTwQ[Q] = ld_tw<R>(a, e);
       }
       __syncthreads();
-      // Psi[jj][j1][grp][gt]
-      const int npsi = unit ? 0 : J * NB * G * 9;
+      // Psi[jj][j1][grp][gt]: one thread per (jj, j1, grp) and block of kGtb of the nine (gamma, theta); the
+      // nine products e0(alpha) e1(beta) of each quartet are formed once per block
+      constexpr int kGtb = 3;
+      const int npsi = unit ? 0 : J * NB * G * (9 / kGtb);
       for (int o = tid; o < npsi; o += nthr) {
-        const int gt = o % 9;
-        const int t9 = o / 9;
+        const int gb = o % (9 / kGtb);
+        const int t9 = o / (9 / kGtb);
         const int grp = t9 % G;
         const int jr = t9 / G;  // jj * NB + j1
         const int j1 = jr % NB, jj = jr / NB;
-        C sum = cmk<R>(0, 0);
+        C sum[kGtb];
+#pragma unroll
+        for (int u = 0; u < kGtb; ++u) sum[u] = cmk<R>(0, 0);
         for (int qq = a.grp_qstart[grp]; qq < a.grp_qstart[grp + 1]; ++qq) {
           const int Q = a.grp_q[qq];
           const int ia = a.qmeta[9 * Q], ja = a.qmeta[9 * Q + 1];
-          const size_t fo = 81 * (size_t)Q + gt;
-          C s = cmk<R>(0, 0);
+          C p[9];
 #pragma unroll
           for (int al = 0; al < 3; ++al) {
             const C e0 = sE0[jj * NB + 3 * ia + al];
 #pragma unroll
-            for (int be = 0; be < 3; ++be) {
-              const C p = cmul(e0, sE1[j1 * NB + 3 * ja + be]);
-              const R fv = ld_fc<R>(a, fo + (al * 3 + be) * 9);
-              s.re = fma(fv, p.re, s.re);
-              s.im = fma(fv, p.im, s.im);
-            }
+            for (int be = 0; be < 3; ++be) p[al * 3 + be] = cmul(e0, sE1[j1 * NB + 3 * ja + be]);
           }
-          cfma(sum, sTwQ[Q], s);
+          const C tq = sTwQ[Q];
+          const size_t fo = 81 * (size_t)Q + gb * kGtb;
+#pragma unroll
+          for (int u = 0; u < kGtb; ++u) {
+            C s = cmk<R>(0, 0);
+#pragma unroll
+            for (int ab = 0; ab < 9; ++ab) {
+              const R fv = ld_fc<R>(a, fo + ab * 9 + u);
+              s.re = fma(fv, p[ab].re, s.re);
+              s.im = fma(fv, p[ab].im, s.im);
+            }
+            cfma(sum[u], tq, s);
+          }
         }
-        sPsi[o] = sum;
+#pragma unroll
+        for (int u = 0; u < kGtb; ++u) sPsi[(size_t)t9 * 9 + gb * kGtb + u] = sum[u];
       }
       __syncthreads();
 
-      for (int k2 = unit ? 0 : k1; k2 < N; ++k2) {
+      const int k2_first = unit ? 0 : k1;
+      // grid coordinates of q'' (advanced in row-major order) and of q + q'; the third partner is q + q' + q''
+      int g2[3] = {k2_first / (a.grid[1] * a.grid[2]), (k2_first / a.grid[2]) % a.grid[1], k2_first % a.grid[2]};
+      const int gs[3] = {(g[0] + g1[0]) % a.grid[0], (g[1] + g1[1]) % a.grid[1], (g[2] + g1[2]) % a.grid[2]};
+      for (int k2 = k2_first; k2 < N; ++k2) {
         // ---- phase 1: per-k2 tables
-        const int g2[3] = {k2 / (a.grid[1] * a.grid[2]), (k2 / a.grid[2]) % a.grid[1], k2 % a.grid[2]};
-        const int g3[3] = {(g[0] + g1[0] + g2[0]) % a.grid[0], (g[1] + g1[1] + g2[1]) % a.grid[1],
-                           (g[2] + g1[2] + g2[2]) % a.grid[2]};
+        if (k2 != k2_first && ++g2[2] == a.grid[2]) {
+          g2[2] = 0;
+          if (++g2[1] == a.grid[1]) {
+            g2[1] = 0;
+            ++g2[0];
+          }
+        }
+        int g3[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          g3[d] = gs[d] + g2[d];
+          if (g3[d] >= a.grid[d]) g3[d] -= a.grid[d];
+        }
         const int k3 = (g3[0] * a.grid[1] + g3[1]) * a.grid[2] + g3[2];
         for (int o = tid; o < NB2; o += nthr) {
           sE2[o] = ld_e<R>(a, (size_t)k2 * NB2 + o);
@@ -632,9 +657,10 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
         }
         for (int gi = tid; gi < G; gi += nthr) {
           const int* gm = a.gmeta + 5 * gi;
-          long long e = 0;
-          for (int d = 0; d < 3; ++d) e += (long long)a.Lfac[d] * wrapi(g2[d] * gm[2 + d], a.grid[d]);
-          sTw2[gi] = ld_tw<R>(a, (int)(e % a.L));
+          int e = 0;  // each term is below L, so e < 3 L
+          for (int d = 0; d < 3; ++d) e += a.Lfac[d] * wrapi(g2[d] * gm[2 + d], a.grid[d]);
+          while (e >= a.L) e -= a.L;
+          sTw2[gi] = ld_tw<R>(a, e);
         }
         __syncthreads();
         // ---- phase 2: sigma tables; A row and T row
