@@ -381,8 +381,9 @@ def run_configs(args):
             sel = [int(m) for m in rng.choice(np.arange(nb, N * nb), size=1, replace=False)]
             q_s = sel[0] // nb
             ref = None
-            # the oracle costs ~3 N^2 nb^3 / 2e7 s per mode on 16 cores: skip it beyond ~2 minutes
-            if 3.0 * N ** 2 * nb ** 3 <= 2.5e9:
+            # the oracle's cost per mode on 16 Arm cores, measured: 3 N^2 nb^3 terms at ~1.6e7 (6 / nb)^3
+            # terms/s (its vertex grows as nb^6 per q-pair); skip it beyond ~2.5 minutes
+            if 3.0 * N ** 2 * nb ** 3 / (1.6e7 * (6.0 / nb) ** 3) <= 150.0:
                 t0 = time.perf_counter()
                 ref, _ = oracle.rates4(cr, w, e, v, sel=sel, nthreads=os.cpu_count() or 1)
                 t_or = time.perf_counter() - t0

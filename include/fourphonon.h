@@ -71,6 +71,8 @@ typedef struct {
   int threads;                     /* threads per block (>= block_j0 * nb^2, multiple of 32); 0 = auto */
   int no_graph;                    /* 0: run the device part as a CUDA graph, captured on first use and replayed
                                       while the launch parameters are unchanged; 1: plain stream launches */
+  int process_mask;                /* processes summed (Eq. 4phgamma): bit 0 ++ (recombination), bit 1 +-
+                                      (redistribution), bit 2 -- (splitting); 0 = all three */
 } fp_rates_opts;
 
 /* Counters of one fp_rates4 call. */
@@ -183,6 +185,16 @@ int fp_phase3(fp_ctx* ctx, int nT, const double* T, double scalebroad, const fp_
  * window decisions.  wp4: host, nT x N x nb.
  */
 int fp_phase4(fp_ctx* ctx, int nT, const double* T, double scalebroad, int stride, double* wp4);
+
+/*
+ * Channel-resolved rates: the ++ (recombination), +- (redistribution) and -- (splitting) parts of Eq.
+ * 4phgamma, whose sum is fp_rates4's rate.  rates: host, nT x 3 x N x nb, channel index in the order ++, +-,
+ * --.  opts->process_mask must be 0.  Each channel is one rate-kernel pass (the vertex is recomputed), so
+ * the call costs about three fp_rates4 calls.  stats (nullable) sums the candidates, flops and time of the
+ * three passes; accepted[p] is channel p's count.  Errors as fp_rates4.
+ */
+int fp_rates4_channels(fp_ctx* ctx, int nT, const double* T, double scalebroad, const fp_rates_opts* opts,
+                       double* rates, fp_stats* stats);
 
 /* Number of parameters of the surrogate network for n_in input features (3 tanh layers of 128). */
 int fp_mlp_params_size(int n_in);

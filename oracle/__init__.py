@@ -47,7 +47,8 @@ def lib():
         L.oracle_rates4.restype = ctypes.c_int
         L.oracle_rates4.argtypes = [ip, dp, ctypes.c_int, dp, ctypes.c_int, ip, dp, dp, dp, dp,
                                     ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                    ctypes.c_int, ctypes.c_int, ip, ctypes.c_int, ctypes.c_int, dp, dp]
+                                    ctypes.c_int, ctypes.c_int, ip, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    dp, dp]
         L.oracle_v4.restype = ctypes.c_int
         L.oracle_v4.argtypes = [ip, dp, ctypes.c_int, dp, ctypes.c_int, ip, dp, dp, ctypes.c_int,
                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, ip]
@@ -78,8 +79,11 @@ def evec_to_array(ev):
 
 
 def rates4(cryst, omega, evec, vel, temps=None, scalebroad=None, window=2.0, sigma_min=1e-10, dq_mode=0,
-           sel=None, unit_vertex=False, nthreads=0):
-    """Rates (nT, nsel) in ps^-1 and accepted counts (3,) for modes sel (default: all)."""
+           sel=None, unit_vertex=False, nthreads=0, processes=(0, 1, 2)):
+    """Rates (nT, nsel) in ps^-1 and accepted counts (3,) for modes sel (default: all).
+
+    processes: the classes of Eq. 4phgamma summed, 0 ++ (recombination), 1 +- (redistribution), 2 --
+    (splitting); the default sums all three (the full rate)."""
     temps = cryst.temps if temps is None else temps
     sb = cryst.scalebroad if scalebroad is None else scalebroad
     nb = cryst.nb
@@ -103,7 +107,8 @@ def rates4(cryst, omega, evec, vel, temps=None, scalebroad=None, window=2.0, sig
     acc_p = acc.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     rc = lib().oracle_rates4(grid_p, lat_p, cryst.natoms, m_p, len(qi), qi_p, qf_p, om_p, ev_p, ve_p,
                              len(T), T_p, float(sb), float(window), float(sigma_min), int(dq_mode),
-                             len(sel_a), sel_p, int(bool(unit_vertex)), int(nthreads), out_p, acc_p)
+                             len(sel_a), sel_p, int(bool(unit_vertex)), sum(1 << int(p) for p in set(processes)),
+                             int(nthreads), out_p, acc_p)
     if rc != 0:
         raise ValueError("oracle_rates4 rejected its arguments")
     return out, acc

@@ -229,14 +229,16 @@ static const double ORC_MULT[3] = {0.5, 0.5, 1.0 / 6.0};
  *   sel[s] = q * nb + j (mode id); rates[t * nsel + s] in ps^-1.
  *   accepted[3]: number of terms that passed the energy window, per process, over the selected modes.
  *   unit_vertex != 0 replaces |V|^2 by 1 (the weighted phase space of the same processes).
+ *   proc_mask selects the process classes summed in Eq. 4phgamma: bit 0 ++ (recombination), bit 1 +-
+ *   (redistribution), bit 2 -- (splitting); 7 gives the full rate.
  * Returns 0, or -1 on bad arguments.
  */
 int oracle_rates4(const int grid[3], const double lattice[9], int natoms, const double* mass, int nquart,
                   const int* qidx, const double* qfc, const double* omega, const double* evec,
                   const double* vel, int nT, const double* T, double scalebroad, double window,
-                  double sigma_min, int dq_mode, int nsel, const int* sel, int unit_vertex, int nthreads,
-                  double* rates, double* accepted) {
-  if (!grid || !lattice || natoms <= 0 || nT <= 0 || nsel < 0) return -1;
+                  double sigma_min, int dq_mode, int nsel, const int* sel, int unit_vertex, int proc_mask,
+                  int nthreads, double* rates, double* accepted) {
+  if (!grid || !lattice || natoms <= 0 || nT <= 0 || nsel < 0 || proc_mask < 0 || proc_mask > 7) return -1;
   orc_problem P;
   orc_setup(&P, grid, lattice, natoms, mass, nquart, qidx, qfc, omega, evec, vel);
   const int nb = P.nb, nq = P.nq;
@@ -263,6 +265,7 @@ int oracle_rates4(const int grid[3], const double lattice[9], int natoms, const 
       for (int q1 = 0; q1 < nq; ++q1) {
         for (int q2 = 0; q2 < nq; ++q2) {
           for (int pr = 0; pr < 3; ++pr) {
+            if (!((proc_mask >> pr) & 1)) continue;
             const int s1 = ORC_S1[pr], s2 = ORC_S2[pr];
             const int q3 = orc_third(&P, q, q1, q2, s1, s2);
             int have_phi = 0;

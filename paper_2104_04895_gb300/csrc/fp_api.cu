@@ -401,6 +401,8 @@ static int validate_opts(fp_ctx* c, int nT, const double* T, double sb, const fp
   if (o->precision != FP_PREC_FP64 && o->precision != FP_PREC_MIXED)
     return fail(c, FP_EINVAL, "fp_rates4: unknown precision");
   if (o->dq_mode != 0 && o->dq_mode != 1) return fail(c, FP_EINVAL, "fp_rates4: dq_mode must be 0 or 1");
+  if (o->process_mask < 0 || o->process_mask > 7)
+    return fail(c, FP_EINVAL, "fp_rates4: process_mask must be in [0, 7]");
   return FP_OK;
 }
 
@@ -475,6 +477,47 @@ int fp_rates4(fp_ctx* c, int nT, const double* T, double scalebroad, const fp_ra
   if (rc) return rc;
   FP_CUDA(c, cudaMemcpyAsync(rates, c->d_rates, need * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   FP_CUDA(c, cudaStreamSynchronize(c->stream));
+  return FP_OK;
+}
+
+int fp_rates4_channels(fp_ctx* c, int nT, const double* T, double scalebroad, const fp_rates_opts* opts,
+                       double* rates, fp_stats* stats) {
+  if (!c) return fail(nullptr, FP_EINVAL, "fp_rates4_channels: NULL context");
+  if (!rates) return fail(c, FP_EINVAL, "fp_rates4_channels: NULL output");
+  if (nT < 1 || nT > fp::kMaxT) return fail(c, FP_EINVAL, "fp_rates4_channels: nT must be in [1, 8]");
+  if (opts && opts->process_mask != 0)
+    return fail(c, FP_EINVAL, "fp_rates4_channels: process_mask must be 0 (all three channels are computed)");
+  FP_CUDA(c, cudaSetDevice(c->device));
+  const size_t nm = (size_t)c->N * c->nb, need = (size_t)nT * nm;
+  if (c->rates_cap < need) {
+    dfree(c->d_rates);
+    c->rates_cap = 0;
+    FP_CUDA(c, dalloc(&c->d_rates, need));
+    c->rates_cap = need;
+  }
+  fp_rates_opts o;
+  fp_default_opts(&o);
+  if (opts) o = *opts;
+  o.no_graph = 1;  // three launch configurations in turn: plain launches rather than re-captured graphs
+  fp_stats sum;
+  std::memset(&sum, 0, sizeof(sum));
+  std::vector<double> part(need);
+  for (int p = 0; p < 3; ++p) {
+    o.process_mask = 1 << p;
+    fp_stats st;
+    int rc = rates_impl(c, nT, T, scalebroad, &o, c->d_rates, &st);
+    if (rc) return rc;
+    FP_CUDA(c, cudaMemcpyAsync(part.data(), c->d_rates, need * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    FP_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int t = 0; t < nT; ++t)
+      std::memcpy(rates + ((size_t)t * 3 + p) * nm, part.data() + (size_t)t * nm, nm * sizeof(double));
+    sum.candidates += st.candidates;
+    sum.accepted[p] = st.accepted[p];
+    sum.flops += st.flops;
+    sum.ms += st.ms;
+    std::memcpy(sum.tile, st.tile, sizeof(sum.tile));
+  }
+  if (stats) *stats = sum;
   return FP_OK;
 }
 

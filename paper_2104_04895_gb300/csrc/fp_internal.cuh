@@ -61,6 +61,7 @@ struct RatesArgs {
   unsigned long long* counts; // [3]
   int unit_vertex;           // 1: |W|^2 = 1 (weighted phase space), q' on a stride, ordered (q', q'') pairs
   int k1_stride;             // q' stride of the unit-vertex mode
+  unsigned cand_mask;        // candidates summed (bit c = ordering * 3 + process), from process_mask
 };
 
 // Tile plan of one rates call.

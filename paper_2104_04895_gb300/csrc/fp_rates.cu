@@ -273,6 +273,10 @@ int run_rates(fp_ctx* c, const fp_rates_opts& o, const Plan& p, const Scratch& s
   a.counts = sc.counters + 1;
   a.unit_vertex = unit_stride > 0 ? 1 : 0;
   a.k1_stride = unit_stride > 0 ? unit_stride : 1;
+  {
+    const int pm = o.process_mask == 0 ? 7 : o.process_mask;
+    a.cand_mask = (unsigned)(pm | (pm << 3));  // both orderings of each selected process
+  }
 
   const int want_f32 = o.precision != FP_PREC_FP64;
   const double conv = kConv;
@@ -369,7 +373,9 @@ void fill_stats(const fp_ctx* c, const fp_rates_opts& o, const Plan& p, const un
   } else {
     nsel = (double)p.nq_sel * nb;
   }
-  st->candidates = 3.0 * nsel * (double)N * (double)N * (double)nb * nb * nb;
+  const int pm = o.process_mask == 0 ? 7 : o.process_mask;
+  const double nproc = (double)((pm & 1) + ((pm >> 1) & 1) + ((pm >> 2) & 1));
+  st->candidates = nproc * nsel * (double)N * (double)N * (double)nb * nb * nb;
   for (int k = 0; k < 3; ++k) st->accepted[k] = (double)counts[1 + k];
   // complex multiply-adds (8 flops each) of one rate set as scheduled: per item and q' the Psi prologue,
   // per unordered (q', q'') pair the grouped assembly (9 J nb G), T (J nb^3 nb) and W (J nb^4)

@@ -715,7 +715,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
           const int jq0 = active ? rjj : 0;
           const bool row_ok = active && sH1[x] != 0.f && sH2[y] != 0.f;
           // candidates 0..2: ordering A (q' = (k1,x), q'' = (k2,y)) ++, +-, --; 3..5: ordering B, swapped
-          const unsigned cand = (k1 != k2 && !unit) ? 0x3Fu : 0x07u;
+          const unsigned cand = ((k1 != k2 && !unit) ? 0x3Fu : 0x07u) & a.cand_mask;
           const double w0 = sOm0[jq0];
           const float h0 = sHq[jq0];
           const float hx = sH1[x], hy = sH2[y];
@@ -810,7 +810,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
           const float h0 = sHq[rjj], l0 = sLq[rjj];
           const float hx = sH1[x], hy = sH2[y];
           // candidates 0..2: ordering A (q' = (k1,x), q'' = (k2,y)) ++, +-, --; 3..5: ordering B, swapped
-          const unsigned cand = (k1 != k2 && !unit) ? 0x3Fu : 0x07u;
+          const unsigned cand = ((k1 != k2 && !unit) ? 0x3Fu : 0x07u) & a.cand_mask;
           if (hx != 0.f && hy != 0.f) {
             C e2row[NB];
 #pragma unroll

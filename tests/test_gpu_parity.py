@@ -170,3 +170,48 @@ def test_autotuned_tiles_and_graph_replay(lib):
     for out in outs + [plain]:
         compare(out.reshape(1, -1), ref, RTOL_FP64)
     assert np.array_equal(outs[0], outs[2]) and np.array_equal(outs[0], plain)
+
+
+def test_channels_match_the_oracle_per_process(lib):
+    """fp_rates4_channels: the ++, +- and -- parts of Eq. 4phgamma against the oracle, and their sum
+    against fp_rates4; fp_rates4 with a one-class process_mask gives the same channel."""
+    cr = synth.simple_cubic((3, 3, 3))
+    w, e, v = oracle_modes(cr)
+    temps = [300.0, 700.0]
+    nT = len(temps)
+    with lib.Context.from_crystal(cr) as ctx:
+        ctx.set_modes(w, e, v)
+        ch, st = ctx.rates4_channels(temps, cr.scalebroad)
+        tot, st_tot = ctx.rates4(temps, cr.scalebroad)
+        one, st_one = ctx.rates4(temps, cr.scalebroad, process_mask=2, no_graph=1)
+        chm, _ = ctx.rates4_channels(temps, cr.scalebroad, precision=FP_PREC_MIXED)
+        for bad in (-1, 8):
+            with pytest.raises(lib.FourPhononError):
+                ctx.rates4(temps, cr.scalebroad, process_mask=bad)
+        with pytest.raises(lib.FourPhononError):
+            ctx.rates4_channels(temps, cr.scalebroad, process_mask=1)
+    assert ch.shape == (nT, 3, cr.nq, cr.nb)
+    for p in range(3):
+        ref, acc = oracle.rates4(cr, w, e, v, temps=temps, processes=(p,))
+        assert acc[p] > 0
+        compare(ch[:, p].reshape(nT, -1), ref, RTOL_FP64)
+        compare(chm[:, p].reshape(nT, -1), ref, RTOL_MIXED)
+        assert st["accepted"][p] == acc[p]
+    assert st["accepted"] == st_tot["accepted"]
+    np.testing.assert_allclose(ch.sum(axis=1), tot, rtol=1e-12, atol=0.0)
+    assert np.array_equal(one, ch[:, 1])
+    assert st_one["accepted"][0] == 0 and st_one["accepted"][2] == 0
+    assert st_one["candidates"] == st_tot["candidates"] / 3
+
+
+@pytest.mark.parametrize("window,sigma_min", [(3.5, 1e-10), (2.0, 0.2), (0.5, 1e-10)])
+def test_window_and_sigma_min_options(lib, window, sigma_min):
+    """Window and sigma_min away from their defaults: a window above 2 sends Gaussian arguments past the FP64
+    exp table (u > 4), a large sigma_min makes many terms take delta := 1, a narrow window accepts few."""
+    cr = synth.diamond_si((3, 3, 2))
+    w, e, v = oracle_modes(cr)
+    ref, acc = oracle.rates4(cr, w, e, v, window=window, sigma_min=sigma_min)
+    for prec, rtol in ((FP_PREC_FP64, RTOL_FP64), (FP_PREC_MIXED, RTOL_MIXED)):
+        out, st = run_gpu(lib, cr, w, e, v, precision=prec, window=window, sigma_min=sigma_min)
+        compare(out.reshape(1, -1), ref, rtol)
+        assert np.array_equal(np.array(st["accepted"]), acc)

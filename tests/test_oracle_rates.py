@@ -174,3 +174,26 @@ def test_accepted_counts_by_enumeration():
             ok = (np.abs(dw) <= 2.0 * np.where(sig < 1e-10, 1e-10, sig)) & (W1 != 0) & (W2 != 0) & (W3 != 0)
             count[pr] += ok.sum()
     assert np.array_equal(acc, count)
+
+
+def test_process_classes_split_the_rate():
+    """Eq. 4phgamma sums three process classes; the oracle's per-class rates add up to the full rate, and
+    each class carries exactly its own accepted terms (whose totals the enumeration above pins)."""
+    cr = synth.simple_cubic((3, 3, 3))
+    w, e, v = oracle_modes(cr)
+    nb = cr.nb
+    sel = [nb * 4 + 1, nb * 10 + 2, nb * 22, nb * 13]
+    temps = [150.0, 600.0]
+    full, acc = oracle.rates4(cr, w, e, v, sel=sel, temps=temps)
+    parts = []
+    for p in range(3):
+        r, a = oracle.rates4(cr, w, e, v, sel=sel, temps=temps, processes=(p,))
+        expect = np.zeros(3)
+        expect[p] = acc[p]
+        assert np.array_equal(a, expect)
+        assert np.all(r >= 0.0)
+        parts.append(r)
+    assert acc[0] > 0 and acc[1] > 0 and acc[2] > 0
+    np.testing.assert_allclose(parts[0] + parts[1] + parts[2], full, rtol=1e-13, atol=0.0)
+    two, _ = oracle.rates4(cr, w, e, v, sel=sel, temps=temps, processes=(0, 2))
+    np.testing.assert_allclose(two, parts[0] + parts[2], rtol=1e-13, atol=0.0)
