@@ -196,6 +196,30 @@ int fp_phase4(fp_ctx* ctx, int nT, const double* T, double scalebroad, int strid
 int fp_rates4_channels(fp_ctx* ctx, int nT, const double* T, double scalebroad, const fp_rates_opts* opts,
                        double* rates, fp_stats* stats);
 
+/*
+ * Stars of the q-grid (host only, no GPU).  Force constants that obey the crystal's space-group symmetry
+ * (imposed on the IFCs in Sec. 2.3) give equal rates at q-points related by a point-group operation, so one
+ * q-point per star suffices; the paper states no q-point reduction of its own.  rot: nrot integer 3x3
+ * matrices, row-major, acting on the reciprocal-lattice fractional coordinates of q (q = sum_a f_a b_a,
+ * f -> R f); generators suffice, the orbit is closed under them, and time reversal (q -> -q) is always
+ * added.  An op may mix two grid axes only if they have the same number of points.  rep: N ints, out: the
+ * smallest grid index of each point's star; *n_irr: the number of stars.  FP_EINVAL for a non-unimodular op
+ * or one that mixes axes of unequal size.
+ */
+int fp_star_table(const int grid[3], int nrot, const int* rot, int* rep, int* n_irr);
+
+/*
+ * fp_rates4 evaluated on one q-point per star (fp_star_table) and mapped to the whole grid.  The caller
+ * states that the force constants and masses are invariant under the ops; the rates of equivalent q are
+ * then equal.  The rates of a degenerate set of branches (|dw| <= 1e-8 max w) depend on the basis chosen
+ * inside the set, so every rate is returned as the mean over its degenerate set at the star's
+ * representative.  opts: mode_mask and the q range must be unset and dq_mode 0 (dq_mode 1 is not
+ * point-group invariant).  rates: host, nT x N x nb.  *n_irr (nullable): the number of stars evaluated;
+ * stats: those of the rate pass.  Errors as fp_rates4, and FP_EINVAL as fp_star_table.
+ */
+int fp_rates4_irreducible(fp_ctx* ctx, int nrot, const int* rot, int nT, const double* T, double scalebroad,
+                          const fp_rates_opts* opts, double* rates, fp_stats* stats, int* n_irr);
+
 /* Number of parameters of the surrogate network for n_in input features (3 tanh layers of 128). */
 int fp_mlp_params_size(int n_in);
 

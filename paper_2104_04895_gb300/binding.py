@@ -51,7 +51,7 @@ class fp_stats(ctypes.Structure):
 
 
 EXPORTS = ["fp_version", "fp_default_opts", "fp_init", "fp_set_stream", "fp_modes", "fp_set_modes", "fp_rates4",
-           "fp_rates4_channels", "fp_rates4_device", "fp_rates4_noalloc", "fp_autotune", "fp_phase3", "fp_phase4", "fp_mlp_params_size",
+           "fp_rates4_channels", "fp_rates4_irreducible", "fp_star_table", "fp_rates4_device", "fp_rates4_noalloc", "fp_autotune", "fp_phase3", "fp_phase4", "fp_mlp_params_size",
            "fp_mlp_loss_grad", "fp_surrogate_default_opts", "fp_surrogate_fit", "fp_surrogate_rates", "fp_free",
            "fp_last_error"]
 
@@ -116,6 +116,12 @@ def load(path: str | None = None):
     L.fp_rates4_channels.argtypes = [vp, ctypes.c_int, dp, ctypes.c_double, ctypes.POINTER(fp_rates_opts), dp,
                                      ctypes.POINTER(fp_stats)]
     L.fp_rates4_channels.restype = ctypes.c_int
+    ip = ctypes.POINTER(ctypes.c_int)
+    L.fp_star_table.argtypes = [ip, ctypes.c_int, ip, ip, ip]
+    L.fp_star_table.restype = ctypes.c_int
+    L.fp_rates4_irreducible.argtypes = [vp, ctypes.c_int, ip, ctypes.c_int, dp, ctypes.c_double,
+                                        ctypes.POINTER(fp_rates_opts), dp, ctypes.POINTER(fp_stats), ip]
+    L.fp_rates4_irreducible.restype = ctypes.c_int
     L.fp_rates4_device.restype = ctypes.c_int
     L.fp_rates4_noalloc.argtypes = [vp, ctypes.c_int, dp, ctypes.c_double, ctypes.POINTER(fp_rates_opts), vp,
                                     ctypes.POINTER(fp_stats)]
@@ -267,6 +273,22 @@ class Context:
         del keep
         return out, st.as_dict()
 
+    def rates4_irreducible(self, ops, temps, scalebroad=1.0, **opts):
+        """fp_rates4_irreducible: rates (nT, N, nb) from one q per star of the integer point-group ops
+        (nops, 3, 3) on reciprocal fractional coordinates; returns (rates, stats, number of stars)."""
+        R = np.ascontiguousarray(ops, np.int32).reshape(-1, 9)
+        T = np.ascontiguousarray(temps, np.float64).reshape(-1)
+        o, keep = self.make_opts(**opts)
+        out = np.zeros((len(T), self.N, self.nb))
+        st = fp_stats()
+        nirr = ctypes.c_int(0)
+        rc = self.L.fp_rates4_irreducible(self.h, len(R), R.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(T),
+                                          _dp(T), float(scalebroad), ctypes.byref(o), _dp(out), ctypes.byref(st),
+                                          ctypes.byref(nirr))
+        _check(self.L, self.h, rc)
+        del keep
+        return out, st.as_dict(), nirr.value
+
     def rates4_channels(self, temps, scalebroad=1.0, **opts):
         """fp_rates4_channels: rates (nT, 3, N, nb) of the ++, +- and -- processes."""
         T = np.ascontiguousarray(temps, np.float64).reshape(-1)
@@ -357,3 +379,17 @@ def mlp_loss_grad(X, y, params, device=0):
     if rc != FP_OK:
         raise FourPhononError(rc, "fp_mlp_loss_grad failed")
     return float(loss[0]), g
+
+
+def star_table(grid, ops):
+    """fp_star_table (host only): (rep (N,), number of stars) for the integer ops (nops, 3, 3)."""
+    L = load()
+    g = np.ascontiguousarray(grid, np.int32).reshape(3)
+    R = np.ascontiguousarray(ops, np.int32).reshape(-1, 9)
+    rep = np.zeros(int(np.prod(g)), np.int32)
+    n = ctypes.c_int(0)
+    ip = ctypes.POINTER(ctypes.c_int)
+    rc = L.fp_star_table(g.ctypes.data_as(ip), len(R), R.ctypes.data_as(ip), rep.ctypes.data_as(ip), ctypes.byref(n))
+    if rc != FP_OK:
+        raise FourPhononError(rc, "fp_star_table rejected the operations")
+    return rep, n.value

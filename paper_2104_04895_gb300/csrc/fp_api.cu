@@ -1,4 +1,5 @@
 // C-ABI of libfourphonon: context, validation, device memory, launches (see include/fourphonon.h).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -140,6 +141,7 @@ void fp_free(fp_ctx* c) {
   dfree(c->d_flag);
   dfree(c->d_scratch);
   dfree(c->d_rates);
+  dfree(c->d_star);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
@@ -477,6 +479,89 @@ int fp_rates4(fp_ctx* c, int nT, const double* T, double scalebroad, const fp_ra
   if (rc) return rc;
   FP_CUDA(c, cudaMemcpyAsync(rates, c->d_rates, need * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   FP_CUDA(c, cudaStreamSynchronize(c->stream));
+  return FP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// rate of (q, j) := the mean over the degenerate set of j at the representative of q's star
+__global__ void star_gather_kernel(const double* __restrict__ in, const int* __restrict__ rep,
+                                   const double* __restrict__ omega, int N, int nb, int nT, double tol,
+                                   double* __restrict__ out) {
+  const long long n = (long long)nT * N * nb;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(i % nb);
+    const long long tq = i / nb;
+    const int q = (int)(tq % N), t = (int)(tq / N);
+    const int r = rep[q];
+    const double* w = omega + (size_t)r * nb;
+    int lo = j, hi = j;
+    while (lo > 0 && w[lo] - w[lo - 1] <= tol) --lo;
+    while (hi < nb - 1 && w[hi + 1] - w[hi] <= tol) ++hi;
+    const double* src = in + ((size_t)t * N + r) * nb;
+    double s = 0.0;
+    for (int k = lo; k <= hi; ++k) s += src[k];
+    out[i] = s / (double)(hi - lo + 1);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int fp_rates4_irreducible(fp_ctx* c, int nrot, const int* rot, int nT, const double* T, double scalebroad,
+                          const fp_rates_opts* opts, double* rates, fp_stats* stats, int* n_irr) {
+  if (!c) return fail(nullptr, FP_EINVAL, "fp_rates4_irreducible: NULL context");
+  if (!rates) return fail(c, FP_EINVAL, "fp_rates4_irreducible: NULL output");
+  if (nT < 1 || nT > fp::kMaxT) return fail(c, FP_EINVAL, "fp_rates4_irreducible: nT must be in [1, 8]");
+  if (!c->have_modes) return fail(c, FP_ESTATE, "fp_rates4_irreducible: call fp_modes or fp_set_modes first");
+  if (opts && (opts->mode_mask || opts->q_begin != 0 || opts->q_end > 0))
+    return fail(c, FP_EINVAL, "fp_rates4_irreducible: mode_mask and the q range are set by the star table");
+  if (opts && opts->dq_mode != 0)
+    return fail(c, FP_EINVAL, "fp_rates4_irreducible: dq_mode 1 is not point-group invariant");
+  const int N = c->N, nb = c->nb;
+  const size_t nm = (size_t)N * nb, need = (size_t)nT * nm;
+  std::vector<int> rep(N);
+  int nirr = 0;
+  if (fp_star_table(c->grid, nrot, rot, rep.data(), &nirr) != FP_OK)
+    return fail(c, FP_EINVAL, "fp_rates4_irreducible: an op is not unimodular or mixes grid axes of unequal size");
+  std::vector<unsigned char> mask(nm, 0);
+  for (int q = 0; q < N; ++q)
+    if (rep[q] == q) std::memset(mask.data() + (size_t)q * nb, 1, nb);
+  // degenerate sets as in the modes: |dw| <= 1e-8 max w
+  std::vector<double> w(nm);
+  FP_CUDA(c, cudaSetDevice(c->device));
+  FP_CUDA(c, cudaMemcpyAsync(w.data(), c->d_omega, nm * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  FP_CUDA(c, cudaStreamSynchronize(c->stream));
+  double wmax = 0.0;
+  for (double x : w) wmax = x > wmax ? x : wmax;
+  if (c->rates_cap < 2 * need) {
+    dfree(c->d_rates);
+    c->rates_cap = 0;
+    FP_CUDA(c, dalloc(&c->d_rates, 2 * need));
+    c->rates_cap = 2 * need;
+  }
+  if (c->star_cap < (size_t)N) {
+    dfree(c->d_star);
+    c->star_cap = 0;
+    FP_CUDA(c, dalloc(&c->d_star, (size_t)N));
+    c->star_cap = (size_t)N;
+  }
+  fp_rates_opts o;
+  fp_default_opts(&o);
+  if (opts) o = *opts;
+  o.mode_mask = mask.data();
+  int rc = rates_impl(c, nT, T, scalebroad, &o, c->d_rates, stats);
+  if (rc) return rc;
+  FP_CUDA(c, cudaMemcpyAsync(c->d_star, rep.data(), (size_t)N * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  star_gather_kernel<<<(unsigned)std::min<size_t>((need + 255) / 256, 4096), 256, 0, c->stream>>>(
+      c->d_rates, c->d_star, c->d_omega, N, nb, nT, 1e-8 * wmax, c->d_rates + need);
+  FP_CUDA(c, cudaGetLastError());
+  FP_CUDA(c, cudaMemcpyAsync(rates, c->d_rates + need, need * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  FP_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (n_irr) *n_irr = nirr;
   return FP_OK;
 }
 

@@ -125,6 +125,8 @@ struct fp_ctx {
   size_t scratch_cap = 0;
   double* d_rates = nullptr;
   size_t rates_cap = 0;
+  int* d_star = nullptr;  // star representatives (fp_rates4_irreducible)
+  size_t star_cap = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // tiles chosen by fp_autotune, per (precision, one or several temperatures): J, k1 tile, threads
   int tuned[2][2][3] = {{{0, 0, 0}, {0, 0, 0}}, {{0, 0, 0}, {0, 0, 0}}};

@@ -16,7 +16,9 @@
 //   W[j0][j1][j2][j3]       = sum_{(k g)} e_{kg}(k2,j2) T[..][(k g)][j3]
 // Groups collect quartets with equal (atom k, atom l, D = R_k - R_l).  Thread r < J*nb^2 owns the row
 // (j0, j1, c) when it builds A and T (registers -> shared T) and the row (j0, j1 = x, j2 = y) when it
-// builds W (registers) and screens the nb entries (x, y, j3) of that row, so W never leaves registers.
+// screens the nb entries (x, y, j3) of that row and builds W (registers) where a candidate is accepted.
+// The FP64 path then hands each accepted term to a per-warp queue that the warp evaluates 32 at a time;
+// the FP32 path evaluates a lane's accepted terms in that lane.
 //
 // Window and Gaussian (Sec. 2.4): the decision |dw| <= window * max(sigma, sigma_min) is the FP64 one,
 // with dw = ((w0 +- w') +- w'') - w''' and sigma = (sb * sqrt((dx^2 + dy^2) + dz^2)) * dq evaluated in that
@@ -26,7 +28,7 @@
 // sigma < sigma_min.
 //
 // Precision of the two instantiations:
-//   double: vertex, sigma, dw, Gaussian, Bose weights and sums in FP64.
+//   double: vertex, sigma, dw, Gaussian (table-driven exp), Bose weights and sums in FP64.
 //   float:  vertex assembly and contraction in FP32; dw from two-float frequencies (error-free sums,
 //           |error| <= 2^-44 sum(w)); sigma from two-float velocities; Gaussian and Bose weights in FP32;
 //           compensated (two-float) per-thread sums, FP64 across threads and work items.
@@ -707,10 +709,9 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
         }
         __syncthreads();
         if constexpr (kF64) {
-        // ---- phase 3 (FP64 path): every lane screens the window of its row (jj, x, y) for all j3; the accepted
-        // (entry, candidate) terms enter a per-warp queue and the warp evaluates them 32 at a time, so the
-        // Gaussian and Bose arithmetic runs on full warps however unevenly the accepted terms fall on lanes
-        {
+          // ---- phase 3 (FP64 path): every lane screens the window of its row (jj, x, y) for all j3; the accepted
+          // (entry, candidate) terms enter a per-warp queue and the warp evaluates them 32 at a time, so the
+          // Gaussian and Bose arithmetic runs on full warps however unevenly the accepted terms fall on lanes
           const int x = rj1, y = rc;
           const int jq0 = active ? rjj : 0;
           const bool row_ok = active && sH1[x] != 0.f && sH2[y] != 0.f;
@@ -801,109 +802,108 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
             consume(sQW[qbase + sl], sQI[qbase + sl]);
           }
           __syncwarp();
-        }
         } else {
-        // ---- phase 3 (FP32 path): W row (jj, x, y) in registers, then window, Gaussian and Bose weights
-        if (active) {
-          const int x = rj1, y = rc;
-          const double w0 = sOm0[rjj];
-          const float h0 = sHq[rjj], l0 = sLq[rjj];
-          const float hx = sH1[x], hy = sH2[y];
-          // candidates 0..2: ordering A (q' = (k1,x), q'' = (k2,y)) ++, +-, --; 3..5: ordering B, swapped
-          const unsigned cand = ((k1 != k2 && !unit) ? 0x3Fu : 0x07u) & a.cand_mask;
-          if (hx != 0.f && hy != 0.f) {
-            C e2row[NB];
+          // ---- phase 3 (FP32 path): W row (jj, x, y) in registers, then window, Gaussian and Bose weights
+          if (active) {
+            const int x = rj1, y = rc;
+            const double w0 = sOm0[rjj];
+            const float h0 = sHq[rjj], l0 = sLq[rjj];
+            const float hx = sH1[x], hy = sH2[y];
+            // candidates 0..2: ordering A (q' = (k1,x), q'' = (k2,y)) ++, +-, --; 3..5: ordering B, swapped
+            const unsigned cand = ((k1 != k2 && !unit) ? 0x3Fu : 0x07u) & a.cand_mask;
+            if (hx != 0.f && hy != 0.f) {
+              C e2row[NB];
 #pragma unroll
-            for (int c = 0; c < NB; ++c) e2row[c] = sE2[y * NB + c];
-            const C* tb = sT + (size_t)(rjj * NB + x) * (NB2 + 1);
-            const float ap = h0 + hx, am = h0 - hx, bp = h0 + hy, bm = h0 - hy;
-            const float apy = ap + hy, apm = ap - hy, amm = am - hy;
-            const float bpx = bp + hx, bpm = bp - hx, bmm = bm - hx;
-            const float s0 = (h0 + hx) + hy;
-            // one temperature: the four distinct products c_p (1/(n0 w0)) x leg weights of this row, per
-            // candidate class (++ both orderings, +- ordering A, +- ordering B, -- both orderings)
-            float wpp = 0.f, wpa = 0.f, wpb = 0.f, wmm = 0.f;
-            if constexpr (MAXT == 1) {
-              const float f0 = sF0[rjj], a1 = sF1[2 * x], b1 = sF1[2 * x + 1], a2 = sF2[2 * y], b2 = sF2[2 * y + 1];
-              wpp = 0.5f * f0 * (a1 * a2);
-              wpa = 0.5f * f0 * (a1 * b2);
-              wpb = 0.5f * f0 * (a2 * b1);
-              wmm = (1.0f / 6.0f) * f0 * (b1 * b2);
-            }
-            const float2* PA0 = sSigPM + 0 * NB2 + y * NB;
-            const float2* PA1 = sSigPM + 1 * NB2 + y * NB;
-            const float2* PB0 = sSigPM + 2 * NB2 + x * NB;
-            const float2* PB1 = sSigPM + 3 * NB2 + x * NB;
-#pragma unroll 1
-            for (int j3 = 0; j3 < NB; ++j3) {
-              const float h3 = sH3[j3];
-              if (h3 == 0.f) continue;
-              const float sS = kRelS * (s0 + h3);
-              const float2 a0 = PA0[j3], a1 = PA1[j3], b0 = PB0[j3], b1 = PB1[j3];
-              unsigned accm = 0, band = 0;
-              FP_WINDOW_TEST()
-              if (!accm) continue;
-              C Wv = cmk<R>(unit ? 1 : 0, 0);
-              if (!unit) {
-#pragma unroll
-                for (int c = 0; c < NB; ++c) cfma(Wv, e2row[c], tb[c * NB + j3]);
+              for (int c = 0; c < NB; ++c) e2row[c] = sE2[y * NB + c];
+              const C* tb = sT + (size_t)(rjj * NB + x) * (NB2 + 1);
+              const float ap = h0 + hx, am = h0 - hx, bp = h0 + hy, bm = h0 - hy;
+              const float apy = ap + hy, apm = ap - hy, amm = am - hy;
+              const float bpx = bp + hx, bpm = bp - hx, bmm = bm - hx;
+              const float s0 = (h0 + hx) + hy;
+              // one temperature: the four distinct products c_p (1/(n0 w0)) x leg weights of this row, per
+              // candidate class (++ both orderings, +- ordering A, +- ordering B, -- both orderings)
+              float wpp = 0.f, wpa = 0.f, wpb = 0.f, wmm = 0.f;
+              if constexpr (MAXT == 1) {
+                const float f0 = sF0[rjj], a1 = sF1[2 * x], b1 = sF1[2 * x + 1], a2 = sF2[2 * y], b2 = sF2[2 * y + 1];
+                wpp = 0.5f * f0 * (a1 * a2);
+                wpa = 0.5f * f0 * (a1 * b2);
+                wpb = 0.5f * f0 * (a2 * b1);
+                wmm = (1.0f / 6.0f) * f0 * (b1 * b2);
               }
-              const float W2 = Wv.re * Wv.re + Wv.im * Wv.im;
-              while (accm) {
-                const int c = __ffs(accm) - 1;
-                accm &= accm - 1;
-                const int p = c % 3;
-                cnt0 += (p == 0);
-                cnt1 += (p == 1);
-                cnt2 += (p == 2);
-                const bool ordA = c < 3;
-                const int tab = (c < 3) ? (c == 0 ? 0 : 1) : (c == 3 ? 2 : 3);
-                const int ent = tab * NB2 + (ordA ? y : x) * NB + j3;
-                // Bose selectors: leg q' takes (1+n)/w unless --, leg q'' takes (1+n)/w only for ++
-                const int s1 = (p == 2) ? 1 : 0, s2 = (p == 0) ? 0 : 1;
-                const int i1 = ordA ? x : y, i2 = ordA ? y : x;
-                // dw from two-float frequencies with error-free sums
-                const float fh = ordA ? hx : hy, fl = ordA ? sL1[x] : sL2[y];
-                const float sh = ordA ? hy : hx, sl = ordA ? sL2[y] : sL1[x];
-                const float sg1 = (p == 2) ? -1.f : 1.f, sg2 = (p == 0) ? 1.f : -1.f;
-                float t0, e1, e2, e3;
-                two_sum(h0, sg1 * fh, t0, e1);
-                two_sum(t0, sg2 * sh, t0, e2);
-                two_sum(t0, -h3, t0, e3);
-                const float lo = (((l0 + sg1 * fl) + sg2 * sl) - sL3[j3]) + ((e1 + e2) + e3);
-                const float dwf = t0 + lo;
-                const float inv = sSigI[ent];
-                float delta = 1.0f;
-                if (inv >= 0.f) {
-                  const float xx = dwf * inv;
-                  delta = __expf(-xx * xx) * inv * (float)kInvSqrtPi;
-                }
-                if constexpr (MAXT == 1) {
-                  const float wsel = (p == 0) ? wpp : (p == 2) ? wmm : ordA ? wpa : wpb;
-                  const float term = (W2 * delta) * wsel * sF3[j3];
-                  float s, e;
-                  two_sum(acch[0][0], term, s, e);
-                  acch[0][0] = s;
-                  accl[0][0] += e;
-                } else {
-                  const float base = ((p == 2) ? (1.0f / 6.0f) : 0.5f) * W2 * delta;
-                  const float* fq1 = ordA ? sF1 : sF2;
-                  const float* fq2 = ordA ? sF2 : sF1;
+              const float2* PA0 = sSigPM + 0 * NB2 + y * NB;
+              const float2* PA1 = sSigPM + 1 * NB2 + y * NB;
+              const float2* PB0 = sSigPM + 2 * NB2 + x * NB;
+              const float2* PB1 = sSigPM + 3 * NB2 + x * NB;
+#pragma unroll 1
+              for (int j3 = 0; j3 < NB; ++j3) {
+                const float h3 = sH3[j3];
+                if (h3 == 0.f) continue;
+                const float sS = kRelS * (s0 + h3);
+                const float2 a0 = PA0[j3], a1 = PA1[j3], b0 = PB0[j3], b1 = PB1[j3];
+                unsigned accm = 0, band = 0;
+                FP_WINDOW_TEST()
+                if (!accm) continue;
+                C Wv = cmk<R>(unit ? 1 : 0, 0);
+                if (!unit) {
 #pragma unroll
-                  for (int t = 0; t < MAXT; ++t) {
-                    if (t >= nT) break;
-                    const float term = base * sF0[t * J + rjj] * fq1[2 * (t * NB + i1) + s1] *
-                                       fq2[2 * (t * NB + i2) + s2] * sF3[t * NB + j3];
+                  for (int c = 0; c < NB; ++c) cfma(Wv, e2row[c], tb[c * NB + j3]);
+                }
+                const float W2 = Wv.re * Wv.re + Wv.im * Wv.im;
+                while (accm) {
+                  const int c = __ffs(accm) - 1;
+                  accm &= accm - 1;
+                  const int p = c % 3;
+                  cnt0 += (p == 0);
+                  cnt1 += (p == 1);
+                  cnt2 += (p == 2);
+                  const bool ordA = c < 3;
+                  const int tab = (c < 3) ? (c == 0 ? 0 : 1) : (c == 3 ? 2 : 3);
+                  const int ent = tab * NB2 + (ordA ? y : x) * NB + j3;
+                  // Bose selectors: leg q' takes (1+n)/w unless --, leg q'' takes (1+n)/w only for ++
+                  const int s1 = (p == 2) ? 1 : 0, s2 = (p == 0) ? 0 : 1;
+                  const int i1 = ordA ? x : y, i2 = ordA ? y : x;
+                  // dw from two-float frequencies with error-free sums
+                  const float fh = ordA ? hx : hy, fl = ordA ? sL1[x] : sL2[y];
+                  const float sh = ordA ? hy : hx, sl = ordA ? sL2[y] : sL1[x];
+                  const float sg1 = (p == 2) ? -1.f : 1.f, sg2 = (p == 0) ? 1.f : -1.f;
+                  float t0, e1, e2, e3;
+                  two_sum(h0, sg1 * fh, t0, e1);
+                  two_sum(t0, sg2 * sh, t0, e2);
+                  two_sum(t0, -h3, t0, e3);
+                  const float lo = (((l0 + sg1 * fl) + sg2 * sl) - sL3[j3]) + ((e1 + e2) + e3);
+                  const float dwf = t0 + lo;
+                  const float inv = sSigI[ent];
+                  float delta = 1.0f;
+                  if (inv >= 0.f) {
+                    const float xx = dwf * inv;
+                    delta = __expf(-xx * xx) * inv * (float)kInvSqrtPi;
+                  }
+                  if constexpr (MAXT == 1) {
+                    const float wsel = (p == 0) ? wpp : (p == 2) ? wmm : ordA ? wpa : wpb;
+                    const float term = (W2 * delta) * wsel * sF3[j3];
                     float s, e;
-                    two_sum(acch[0][t], term, s, e);
-                    acch[0][t] = s;
-                    accl[0][t] += e;
+                    two_sum(acch[0][0], term, s, e);
+                    acch[0][0] = s;
+                    accl[0][0] += e;
+                  } else {
+                    const float base = ((p == 2) ? (1.0f / 6.0f) : 0.5f) * W2 * delta;
+                    const float* fq1 = ordA ? sF1 : sF2;
+                    const float* fq2 = ordA ? sF2 : sF1;
+#pragma unroll
+                    for (int t = 0; t < MAXT; ++t) {
+                      if (t >= nT) break;
+                      const float term = base * sF0[t * J + rjj] * fq1[2 * (t * NB + i1) + s1] *
+                                         fq2[2 * (t * NB + i2) + s2] * sF3[t * NB + j3];
+                      float s, e;
+                      two_sum(acch[0][t], term, s, e);
+                      acch[0][t] = s;
+                      accl[0][t] += e;
+                    }
                   }
                 }
               }
             }
           }
-        }
         }
         __syncthreads();
       }

@@ -209,11 +209,13 @@ def simple_cubic(grid=(4, 4, 4), seed_index=1, symmetric=False, temps=(300.0,), 
     bonds = _bonds_unordered(lattice, frac, lambda i, j, d, r: abs(r - a) < 1e-6, a)
     rng = np.random.Generator(np.random.PCG64(SEED_BASE + seed_index))
     K = _draw_tensors(rng, len(bonds))
+    extra = {}
     if symmetric:
         K = _point_group_tensors([b[3] for b in bonds], K, _signed_perms())
+        extra["point_group"] = _signed_perms()
     i4, v4 = _fc4_from_bonds(bonds, K)
     return Crystal("simple-cubic" + ("-sym" if symmetric else ""), lattice, frac, mass, i2, v2, i4, v4,
-                   tuple(grid), tuple(temps), scalebroad)
+                   tuple(grid), tuple(temps), scalebroad, extra)
 
 
 def _fcc_two_atom(a, masses, name, grid, seed_index, symmetric, temps, scalebroad):
@@ -228,14 +230,16 @@ def _fcc_two_atom(a, masses, name, grid, seed_index, symmetric, temps, scalebroa
     bonds = _bonds_unordered(lattice, frac, lambda i, j, d, r: abs(r - r1) < 1e-6, r1)
     rng = np.random.Generator(np.random.PCG64(SEED_BASE + seed_index))
     K = _draw_tensors(rng, len(bonds))
+    extra = {}
     if symmetric:
         vecs = [b[3] for b in bonds]
         ops = [g for g in _signed_perms()
                if all(any(np.allclose(g @ d, e, atol=1e-8) for e in vecs) for d in vecs)]
         K = _point_group_tensors(vecs, K, ops)
+        extra["point_group"] = ops
     i4, v4 = _fc4_from_bonds(bonds, K)
     return Crystal(name + ("-sym" if symmetric else ""), lattice, frac, mass, i2, v2, i4, v4,
-                   tuple(grid), tuple(temps), scalebroad)
+                   tuple(grid), tuple(temps), scalebroad, extra)
 
 
 def diamond_si(grid=(8, 8, 8), seed_index=2, symmetric=False, temps=(300.0,), scalebroad=1.0):
@@ -296,6 +300,24 @@ def licoo2(grid=(10, 10, 6), seed_index=4, temps=(300.0, 500.0, 700.0), scalebro
 
 
 TEMPS_SWEEP = tuple(float(t) for t in range(300, 1001, 100))
+
+
+def point_group_ops(cryst: Crystal) -> np.ndarray:
+    """The Cartesian point-group operations a symmetric crystal was built with, as integer matrices acting on
+    the reciprocal-lattice fractional coordinates of q (q = f @ B with B the reciprocal vectors as rows):
+    R = B^-T g B^T.  Shape (nops, 3, 3), int32."""
+    ops = cryst.extra.get("point_group")
+    if ops is None:
+        raise ValueError(f"{cryst.name} was not built with point-group symmetric force constants")
+    B = 2.0 * np.pi * np.linalg.inv(cryst.lattice).T
+    out = []
+    for g in ops:
+        R = np.linalg.inv(B.T) @ g @ B.T
+        Ri = np.rint(R)
+        if not np.allclose(R, Ri, atol=1e-9):
+            raise ValueError("operation is not a lattice symmetry")
+        out.append(Ri.astype(np.int32))
+    return np.asarray(out, dtype=np.int32)
 
 
 def workload(index: int) -> Crystal:

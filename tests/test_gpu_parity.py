@@ -215,3 +215,45 @@ def test_window_and_sigma_min_options(lib, window, sigma_min):
         out, st = run_gpu(lib, cr, w, e, v, precision=prec, window=window, sigma_min=sigma_min)
         compare(out.reshape(1, -1), ref, rtol)
         assert np.array_equal(np.array(st["accepted"]), acc)
+
+
+def degenerate_mean(rates, omega):
+    """rates (nT, N, nb) averaged over each q's degenerate branch sets (|dw| <= 1e-8 max w, chained)."""
+    out = np.array(rates, dtype=np.float64, copy=True)
+    tol = 1e-8 * np.max(omega)
+    nb = omega.shape[1]
+    for q in range(omega.shape[0]):
+        j = 0
+        while j < nb:
+            k = j
+            while k + 1 < nb and omega[q, k + 1] - omega[q, k] <= tol:
+                k += 1
+            out[:, q, j:k + 1] = rates[:, q, j:k + 1].mean(axis=1, keepdims=True)
+            j = k + 1
+    return out
+
+
+@pytest.mark.parametrize("maker", [lambda: synth.simple_cubic((4, 4, 4), symmetric=True),
+                                   lambda: synth.diamond_si((4, 4, 4), symmetric=True)],
+                         ids=["sc-sym-4x4x4", "diamond-sym-4x4x4"])
+def test_irreducible_wedge_matches_the_full_grid(lib, maker):
+    """fp_rates4_irreducible on point-group symmetric force constants: one q per star, mapped to the grid,
+    equals the full-grid rates averaged over degenerate sets."""
+    cr = maker()
+    w, e, v = oracle_modes(cr)
+    ops = synth.point_group_ops(cr)
+    temps = [300.0, 600.0]
+    with lib.Context.from_crystal(cr) as ctx:
+        ctx.set_modes(w, e, v)
+        full, st_full = ctx.rates4(temps, cr.scalebroad)
+        irr, st_irr, nirr = ctx.rates4_irreducible(ops, temps, cr.scalebroad)
+        irr_m, _, _ = ctx.rates4_irreducible(ops, temps, cr.scalebroad, precision=FP_PREC_MIXED)
+        with pytest.raises(lib.FourPhononError):
+            ctx.rates4_irreducible(ops, temps, cr.scalebroad, dq_mode=1)
+        with pytest.raises(lib.FourPhononError):
+            ctx.rates4_irreducible(ops, temps, cr.scalebroad, q_end=3)
+    assert nirr == lib.star_table(cr.grid, ops)[1] and nirr < cr.nq
+    ref = degenerate_mean(full, np.asarray(w).reshape(cr.nq, cr.nb))
+    compare(irr.reshape(len(temps), -1), ref.reshape(len(temps), -1), 1e-9)
+    compare(irr_m.reshape(len(temps), -1), ref.reshape(len(temps), -1), RTOL_MIXED)
+    assert st_irr["candidates"] == st_full["candidates"] * nirr / cr.nq
