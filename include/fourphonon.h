@@ -73,6 +73,8 @@ typedef struct {
                                       while the launch parameters are unchanged; 1: plain stream launches */
   int process_mask;                /* processes summed (Eq. 4phgamma): bit 0 ++ (recombination), bit 1 +-
                                       (redistribution), bit 2 -- (splitting); 0 = all three */
+  int nu_select;                   /* 0: all processes; 1: normal only; 2: Umklapp only (Sec. 2.2: Q = 0 or not;
+                                      the representatives are described at fp_rates4_nu) */
 } fp_rates_opts;
 
 /* Counters of one fp_rates4 call. */
@@ -195,6 +197,18 @@ int fp_phase4(fp_ctx* ctx, int nT, const double* T, double scalebroad, int strid
  */
 int fp_rates4_channels(fp_ctx* ctx, int nT, const double* T, double scalebroad, const fp_rates_opts* opts,
                        double* rates, fp_stats* stats);
+
+/*
+ * Normal and Umklapp rates (the paper's separate normal and Umklapp RTA rate outputs, Appendix A): a process
+ * q''' = q + s1 q' + s2 q'' + Q is normal when Q = 0 (Sec. 2.2).  Q depends on how each grid wavevector is
+ * represented, which the paper does not state; here each is its shortest translate sum_a (g_a / N_a - m_a) b_a
+ * over integers m_a in [-2, 2], with squared lengths within 1e-9 relative counted as equal and such ties won by
+ * the lexicographically smallest (m_0, m_1, m_2).  rates: host, nT x 2 x N x nb (normal, then Umklapp); their
+ * sum is fp_rates4's rate.  opts->nu_select must be 0; process_mask and the other options apply to both parts.
+ * Two rate-kernel passes.  stats (nullable) sums the passes.  Errors as fp_rates4.
+ */
+int fp_rates4_nu(fp_ctx* ctx, int nT, const double* T, double scalebroad, const fp_rates_opts* opts, double* rates,
+                 fp_stats* stats);
 
 /*
  * Stars of the q-grid (host only, no GPU).  Force constants that obey the crystal's space-group symmetry

@@ -38,7 +38,7 @@ class fp_rates_opts(ctypes.Structure):
                 ("dq_mode", ctypes.c_int), ("mode_mask", ctypes.POINTER(ctypes.c_ubyte)),
                 ("q_begin", ctypes.c_int), ("q_end", ctypes.c_int), ("block_j0", ctypes.c_int),
                 ("k1_tile", ctypes.c_int), ("threads", ctypes.c_int), ("no_graph", ctypes.c_int),
-                ("process_mask", ctypes.c_int)]
+                ("process_mask", ctypes.c_int), ("nu_select", ctypes.c_int)]
 
 
 class fp_stats(ctypes.Structure):
@@ -51,7 +51,7 @@ class fp_stats(ctypes.Structure):
 
 
 EXPORTS = ["fp_version", "fp_default_opts", "fp_init", "fp_set_stream", "fp_modes", "fp_set_modes", "fp_rates4",
-           "fp_rates4_channels", "fp_rates4_irreducible", "fp_star_table", "fp_rates4_device", "fp_rates4_noalloc", "fp_autotune", "fp_phase3", "fp_phase4", "fp_mlp_params_size",
+           "fp_rates4_channels", "fp_rates4_nu", "fp_rates4_irreducible", "fp_star_table", "fp_rates4_device", "fp_rates4_noalloc", "fp_autotune", "fp_phase3", "fp_phase4", "fp_mlp_params_size",
            "fp_mlp_loss_grad", "fp_surrogate_default_opts", "fp_surrogate_fit", "fp_surrogate_rates", "fp_free",
            "fp_last_error"]
 
@@ -116,6 +116,8 @@ def load(path: str | None = None):
     L.fp_rates4_channels.argtypes = [vp, ctypes.c_int, dp, ctypes.c_double, ctypes.POINTER(fp_rates_opts), dp,
                                      ctypes.POINTER(fp_stats)]
     L.fp_rates4_channels.restype = ctypes.c_int
+    L.fp_rates4_nu.argtypes = L.fp_rates4_channels.argtypes
+    L.fp_rates4_nu.restype = ctypes.c_int
     ip = ctypes.POINTER(ctypes.c_int)
     L.fp_star_table.argtypes = [ip, ctypes.c_int, ip, ip, ip]
     L.fp_star_table.restype = ctypes.c_int
@@ -250,13 +252,14 @@ class Context:
 
     @staticmethod
     def make_opts(precision=FP_PREC_FP64, window=2.0, sigma_min=1e-10, dq_mode=0, mode_mask=None, q_begin=0,
-                  q_end=0, block_j0=0, k1_tile=0, threads=0, no_graph=0, process_mask=0):
+                  q_end=0, block_j0=0, k1_tile=0, threads=0, no_graph=0, process_mask=0, nu_select=0):
         o = fp_rates_opts()
         o.precision, o.window, o.sigma_min, o.dq_mode = int(precision), float(window), float(sigma_min), int(dq_mode)
         o.q_begin, o.q_end, o.block_j0, o.k1_tile, o.threads = int(q_begin), int(q_end), int(block_j0), \
             int(k1_tile), int(threads)
         o.no_graph = int(no_graph)
         o.process_mask = int(process_mask)
+        o.nu_select = int(nu_select)
         keep = None
         if mode_mask is not None:
             keep = np.ascontiguousarray(mode_mask, np.uint8)
@@ -288,6 +291,17 @@ class Context:
         _check(self.L, self.h, rc)
         del keep
         return out, st.as_dict(), nirr.value
+
+    def rates4_nu(self, temps, scalebroad=1.0, **opts):
+        """fp_rates4_nu: rates (nT, 2, N, nb) of normal and Umklapp processes."""
+        T = np.ascontiguousarray(temps, np.float64).reshape(-1)
+        o, keep = self.make_opts(**opts)
+        out = np.zeros((len(T), 2, self.N, self.nb))
+        st = fp_stats()
+        rc = self.L.fp_rates4_nu(self.h, len(T), _dp(T), float(scalebroad), ctypes.byref(o), _dp(out), ctypes.byref(st))
+        _check(self.L, self.h, rc)
+        del keep
+        return out, st.as_dict()
 
     def rates4_channels(self, temps, scalebroad=1.0, **opts):
         """fp_rates4_channels: rates (nT, 3, N, nb) of the ++, +- and -- processes."""

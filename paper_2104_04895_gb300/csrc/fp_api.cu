@@ -142,6 +142,7 @@ void fp_free(fp_ctx* c) {
   dfree(c->d_scratch);
   dfree(c->d_rates);
   dfree(c->d_star);
+  dfree(c->d_bzm);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
@@ -317,7 +318,13 @@ int fp_init(fp_ctx** out, const double lattice[9], int natoms, const double* fra
   INIT_CUDA(dalloc(&c->d_tw, (size_t)c->L));
   INIT_CUDA(fp::launch_twiddles(c, s));
   INIT_CUDA(dalloc(&c->d_flag, 1));
-  INIT_CUDA(cudaStreamSynchronize(s));
+  {
+    std::vector<int> bzm(3 * (size_t)c->N);
+    fp::bz_shifts(c->grid, c->rec, bzm.data());
+    INIT_CUDA(dalloc(&c->d_bzm, bzm.size()));
+    INIT_CUDA(cudaMemcpyAsync(c->d_bzm, bzm.data(), bzm.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    INIT_CUDA(cudaStreamSynchronize(s));  // bzm is a local buffer
+  }
   cudaFree(d_atoms4);
 #undef INIT_CUDA
   *out = c;
@@ -405,6 +412,7 @@ static int validate_opts(fp_ctx* c, int nT, const double* T, double sb, const fp
   if (o->dq_mode != 0 && o->dq_mode != 1) return fail(c, FP_EINVAL, "fp_rates4: dq_mode must be 0 or 1");
   if (o->process_mask < 0 || o->process_mask > 7)
     return fail(c, FP_EINVAL, "fp_rates4: process_mask must be in [0, 7]");
+  if (o->nu_select < 0 || o->nu_select > 2) return fail(c, FP_EINVAL, "fp_rates4: nu_select must be 0, 1 or 2");
   return FP_OK;
 }
 
@@ -565,13 +573,17 @@ int fp_rates4_irreducible(fp_ctx* c, int nrot, const int* rot, int nT, const dou
   return FP_OK;
 }
 
-int fp_rates4_channels(fp_ctx* c, int nT, const double* T, double scalebroad, const fp_rates_opts* opts,
-                       double* rates, fp_stats* stats) {
-  if (!c) return fail(nullptr, FP_EINVAL, "fp_rates4_channels: NULL context");
-  if (!rates) return fail(c, FP_EINVAL, "fp_rates4_channels: NULL output");
-  if (nT < 1 || nT > fp::kMaxT) return fail(c, FP_EINVAL, "fp_rates4_channels: nT must be in [1, 8]");
-  if (opts && opts->process_mask != 0)
-    return fail(c, FP_EINVAL, "fp_rates4_channels: process_mask must be 0 (all three channels are computed)");
+}  // extern "C"
+
+namespace {
+
+// npass rate passes, pass p with the options set(o, p), into rates[t][p][N][nb] (host); stats sums the
+// passes' candidates, flops and time, and takes accepted[k] from every pass that counted process k
+int rates_passes(fp_ctx* c, int nT, const double* T, double sb, const fp_rates_opts* opts, int npass,
+                 void (*set)(fp_rates_opts&, int), double* rates, fp_stats* stats, const char* who) {
+  const std::string name(who);
+  if (!rates) return fail(c, FP_EINVAL, name + ": NULL output");
+  if (nT < 1 || nT > fp::kMaxT) return fail(c, FP_EINVAL, name + ": nT must be in [1, 8]");
   FP_CUDA(c, cudaSetDevice(c->device));
   const size_t nm = (size_t)c->N * c->nb, need = (size_t)nT * nm;
   if (c->rates_cap < need) {
@@ -583,21 +595,21 @@ int fp_rates4_channels(fp_ctx* c, int nT, const double* T, double scalebroad, co
   fp_rates_opts o;
   fp_default_opts(&o);
   if (opts) o = *opts;
-  o.no_graph = 1;  // three launch configurations in turn: plain launches rather than re-captured graphs
+  o.no_graph = 1;  // several launch configurations in turn: plain launches rather than re-captured graphs
   fp_stats sum;
   std::memset(&sum, 0, sizeof(sum));
   std::vector<double> part(need);
-  for (int p = 0; p < 3; ++p) {
-    o.process_mask = 1 << p;
+  for (int p = 0; p < npass; ++p) {
+    set(o, p);
     fp_stats st;
-    int rc = rates_impl(c, nT, T, scalebroad, &o, c->d_rates, &st);
+    int rc = rates_impl(c, nT, T, sb, &o, c->d_rates, &st);
     if (rc) return rc;
     FP_CUDA(c, cudaMemcpyAsync(part.data(), c->d_rates, need * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     FP_CUDA(c, cudaStreamSynchronize(c->stream));
     for (int t = 0; t < nT; ++t)
-      std::memcpy(rates + ((size_t)t * 3 + p) * nm, part.data() + (size_t)t * nm, nm * sizeof(double));
+      std::memcpy(rates + ((size_t)t * npass + p) * nm, part.data() + (size_t)t * nm, nm * sizeof(double));
     sum.candidates += st.candidates;
-    sum.accepted[p] = st.accepted[p];
+    for (int k = 0; k < 3; ++k) sum.accepted[k] += st.accepted[k];
     sum.flops += st.flops;
     sum.ms += st.ms;
     std::memcpy(sum.tile, st.tile, sizeof(sum.tile));
@@ -606,4 +618,27 @@ int fp_rates4_channels(fp_ctx* c, int nT, const double* T, double scalebroad, co
   return FP_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int fp_rates4_channels(fp_ctx* c, int nT, const double* T, double scalebroad, const fp_rates_opts* opts,
+                       double* rates, fp_stats* stats) {
+  if (!c) return fail(nullptr, FP_EINVAL, "fp_rates4_channels: NULL context");
+  if (opts && opts->process_mask != 0)
+    return fail(c, FP_EINVAL, "fp_rates4_channels: process_mask must be 0 (all three channels are computed)");
+  return rates_passes(c, nT, T, scalebroad, opts, 3, [](fp_rates_opts& o, int p) { o.process_mask = 1 << p; },
+                      rates, stats, "fp_rates4_channels");
+}
+
+int fp_rates4_nu(fp_ctx* c, int nT, const double* T, double scalebroad, const fp_rates_opts* opts, double* rates,
+                 fp_stats* stats) {
+  if (!c) return fail(nullptr, FP_EINVAL, "fp_rates4_nu: NULL context");
+  if (opts && opts->nu_select != 0)
+    return fail(c, FP_EINVAL, "fp_rates4_nu: nu_select must be 0 (both parts are computed)");
+  return rates_passes(c, nT, T, scalebroad, opts, 2, [](fp_rates_opts& o, int p) { o.nu_select = 1 + p; }, rates,
+                      stats, "fp_rates4_nu");
+}
+
 }  // extern "C"
+

@@ -62,6 +62,8 @@ struct RatesArgs {
   int unit_vertex;           // 1: |W|^2 = 1 (weighted phase space), q' on a stride, ordered (q', q'') pairs
   int k1_stride;             // q' stride of the unit-vertex mode
   unsigned cand_mask;        // candidates summed (bit c = ordering * 3 + process), from process_mask
+  int nu_select;             // 0: all processes, 1: normal only, 2: Umklapp only
+  const int* bzm;            // [N][3] Brillouin-zone shifts of the grid points (normal/Umklapp reading)
 };
 
 // Tile plan of one rates call.
@@ -114,6 +116,7 @@ struct fp_ctx {
   int* d_kl_start = nullptr;
   int* d_kl_grp = nullptr;
   double2* d_tw = nullptr;
+  int* d_bzm = nullptr;  // [N][3] Brillouin-zone shifts (bz_shifts)
   // modes
   bool have_modes = false;
   double* d_omega = nullptr;
@@ -162,6 +165,8 @@ int run_rates(fp_ctx* c, const fp_rates_opts& o, const Plan& p, const Scratch& s
 // Sampled four-phonon weighted phase space of every mode (surrogate feature): the rate sum with |W|^2 = 1
 // over q' on a stride (ordered pairs), scaled to the full grid; d_out: nT x N x nb, mixed precision.
 int phase4_sampled(fp_ctx* c, int nT, const double* T, double sb, int stride, double* d_out, std::string* err);
+// Brillouin-zone shifts of the grid points (fp_sym.cu), N x 3
+void bz_shifts(const int grid[3], const double rec[9], int* out);
 void fill_stats(const fp_ctx* c, const fp_rates_opts& o, const Plan& p, const unsigned long long counts[4],
                 fp_stats* st);
 }  // namespace fp

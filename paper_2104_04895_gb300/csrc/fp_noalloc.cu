@@ -83,6 +83,8 @@ extern "C" int fp_rates4_noalloc(fp_ctx* c, int nT, const double* T, double sb, 
   if (o.dq_mode != 0 && o.dq_mode != 1) return nfail(c, FP_EINVAL, "fp_rates4_noalloc: dq_mode must be 0 or 1");
   if (o.process_mask < 0 || o.process_mask > 7)
     return nfail(c, FP_EINVAL, "fp_rates4_noalloc: process_mask must be in [0, 7]");
+  if (o.nu_select < 0 || o.nu_select > 2)
+    return nfail(c, FP_EINVAL, "fp_rates4_noalloc: nu_select must be 0, 1 or 2");
   if (c->device < 0 || c->device >= kMaxDevices)
     return nfail(c, FP_EINVAL, "fp_rates4_noalloc: device ordinal too large");
   NA_CUDA(c, cudaSetDevice(c->device));

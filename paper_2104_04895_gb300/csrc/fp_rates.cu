@@ -277,6 +277,8 @@ int run_rates(fp_ctx* c, const fp_rates_opts& o, const Plan& p, const Scratch& s
     const int pm = o.process_mask == 0 ? 7 : o.process_mask;
     a.cand_mask = (unsigned)(pm | (pm << 3));  // both orderings of each selected process
   }
+  a.nu_select = o.nu_select;
+  a.bzm = c->d_bzm;
 
   const int want_f32 = o.precision != FP_PREC_FP64;
   const double conv = kConv;

@@ -296,6 +296,37 @@ __device__ __forceinline__ double dw_fp64(int c, double w0, double wx, double wy
 }
 
 // largest block of each branch count (J * nb^2 rows, rounded up to warps); two blocks per SM
+// Umklapp candidates of one (q, k1, k2) triple (k3 = q + k1 + k2): bit c set when candidate c is an Umklapp
+// process (Sec. 2.2: q''' = q + s1 q' + s2 q'' + Q with Q != 0), every wavevector taken as its
+// Brillouin-zone representative g / N - m (a.bzm). The candidates' partners (q', q'') with signs (s1, s2):
+// ++ (k1, k2) or (k2, k1), +- A (k1, -k2), +- B (k2, -k1), -- (-k1, -k2) or (-k2, -k1); the third is always k3.
+__device__ unsigned umklapp_bits(const RatesArgs& a, const int g[3], const int g1[3], const int g2[3],
+                                 const int g3[3]) {
+  int n1[3], n2[3];
+  for (int d = 0; d < 3; ++d) {
+    n1[d] = g1[d] ? a.grid[d] - g1[d] : 0;
+    n2[d] = g2[d] ? a.grid[d] - g2[d] : 0;
+  }
+  auto idx = [&](const int* x) { return (x[0] * a.grid[1] + x[1]) * a.grid[2] + x[2]; };
+  const int* m0 = a.bzm + 3 * idx(g);
+  const int* m3 = a.bzm + 3 * idx(g3);
+  // 1 if q + sa qa + sb qb - k3 in representatives is nonzero
+  auto umk = [&](const int* ga, int sa, const int* gb, int sb) -> unsigned {
+    const int* ma = a.bzm + 3 * idx(ga);
+    const int* mb = a.bzm + 3 * idx(gb);
+    unsigned u = 0;
+    for (int d = 0; d < 3; ++d) {
+      const int n = a.grid[d];
+      const int num = (g[d] - n * m0[d]) + sa * (ga[d] - n * ma[d]) + sb * (gb[d] - n * mb[d]) - (g3[d] - n * m3[d]);
+      u |= num != 0 ? 1u : 0u;
+    }
+    return u;
+  };
+  const unsigned upp = umk(g1, 1, g2, 1), upa = umk(g1, 1, n2, -1), upb = umk(g2, 1, n1, -1);
+  const unsigned umm = umk(n1, -1, n2, -1);
+  return upp | (upa << 1) | (umm << 2) | (upp << 3) | (upb << 4) | (umm << 5);
+}
+
 __host__ __device__ constexpr int max_threads_for(int nb) { return nb == 3 ? 128 : nb == 6 ? 224 : 160; }
 
 // blocks per SM the register budget is sized for (three FP32 blocks measured 11% faster than two on the
@@ -360,6 +391,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
   using C = Cx<R>;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long s_item;
+  __shared__ unsigned s_umask;  // Umklapp candidates of the current (k1, k2)
   const int J = a.J, G = a.G, nT = a.nT, N = a.N;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int rows = J * NB2;
@@ -621,6 +653,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
           if (g3[d] >= a.grid[d]) g3[d] -= a.grid[d];
         }
         const int k3 = (g3[0] * a.grid[1] + g3[1]) * a.grid[2] + g3[2];
+        if (a.nu_select != 0 && tid == 0) s_umask = umklapp_bits(a, g, g1, g2, g3);  // read after the barrier
         for (int o = tid; o < NB2; o += nthr) {
           sE2[o] = ld_e<R>(a, (size_t)k2 * NB2 + o);
           sE3[o] = ld_e<R>(a, (size_t)k3 * NB2 + o);
@@ -716,7 +749,8 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
           const int jq0 = active ? rjj : 0;
           const bool row_ok = active && sH1[x] != 0.f && sH2[y] != 0.f;
           // candidates 0..2: ordering A (q' = (k1,x), q'' = (k2,y)) ++, +-, --; 3..5: ordering B, swapped
-          const unsigned cand = ((k1 != k2 && !unit) ? 0x3Fu : 0x07u) & a.cand_mask;
+          const unsigned cand = ((k1 != k2 && !unit) ? 0x3Fu : 0x07u) & a.cand_mask &
+                                (a.nu_select == 0 ? 0x3Fu : a.nu_select == 1 ? ~s_umask : s_umask);
           const double w0 = sOm0[jq0];
           const float h0 = sHq[jq0];
           const float hx = sH1[x], hy = sH2[y];
@@ -810,7 +844,8 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
             const float h0 = sHq[rjj], l0 = sLq[rjj];
             const float hx = sH1[x], hy = sH2[y];
             // candidates 0..2: ordering A (q' = (k1,x), q'' = (k2,y)) ++, +-, --; 3..5: ordering B, swapped
-            const unsigned cand = ((k1 != k2 && !unit) ? 0x3Fu : 0x07u) & a.cand_mask;
+            const unsigned cand = ((k1 != k2 && !unit) ? 0x3Fu : 0x07u) & a.cand_mask &
+                                  (a.nu_select == 0 ? 0x3Fu : a.nu_select == 1 ? ~s_umask : s_umask);
             if (hx != 0.f && hy != 0.f) {
               C e2row[NB];
 #pragma unroll

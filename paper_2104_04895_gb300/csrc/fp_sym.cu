@@ -68,3 +68,37 @@ extern "C" int fp_star_table(const int grid[3], int nrot, const int* rot, int* r
   *n_irr = count;
   return FP_OK;
 }
+
+namespace fp {
+
+// Brillouin-zone representative of every grid point, for the normal/Umklapp split: the translate
+// sum_a (g_a / N_a - m_a) b_a of smallest length over integer m_a in [-2, 2] (b_a: rows of rec); squared lengths
+// within 1e-9 relative are equal, and then the lexicographically smallest (m_0, m_1, m_2) is taken.
+// out: N x 3 shifts m.
+void bz_shifts(const int grid[3], const double rec[9], int* out) {
+  const int N = grid[0] * grid[1] * grid[2];
+  for (int q = 0; q < N; ++q) {
+    const int g[3] = {q / (grid[1] * grid[2]), (q / grid[2]) % grid[1], q % grid[2]};
+    double best = -1.0;
+    int bm[3] = {0, 0, 0};
+    for (int m0 = -2; m0 <= 2; ++m0)
+      for (int m1 = -2; m1 <= 2; ++m1)
+        for (int m2 = -2; m2 <= 2; ++m2) {
+          const double f[3] = {(double)g[0] / grid[0] - m0, (double)g[1] / grid[1] - m1, (double)g[2] / grid[2] - m2};
+          double len2 = 0.0;
+          for (int c = 0; c < 3; ++c) {
+            const double k = f[0] * rec[c] + f[1] * rec[3 + c] + f[2] * rec[6 + c];
+            len2 += k * k;
+          }
+          if (best < 0.0 || len2 < best * (1.0 - 1e-9)) {  // visited in lexicographic order of m
+            best = len2;
+            bm[0] = m0;
+            bm[1] = m1;
+            bm[2] = m2;
+          }
+        }
+    for (int a = 0; a < 3; ++a) out[3 * q + a] = bm[a];
+  }
+}
+
+}  // namespace fp

@@ -257,3 +257,31 @@ def test_irreducible_wedge_matches_the_full_grid(lib, maker):
     compare(irr.reshape(len(temps), -1), ref.reshape(len(temps), -1), 1e-9)
     compare(irr_m.reshape(len(temps), -1), ref.reshape(len(temps), -1), RTOL_MIXED)
     assert st_irr["candidates"] == st_full["candidates"] * nirr / cr.nq
+
+
+@pytest.mark.parametrize("maker", [lambda: synth.simple_cubic((4, 4, 4)), lambda: synth.diamond_si((3, 3, 2)),
+                                   lambda: synth.licoo2((2, 2, 2))], ids=["sc-4x4x4", "diamond-3x3x2", "licoo2-2x2x2"])
+def test_normal_and_umklapp_match_the_oracle(lib, maker):
+    """fp_rates4_nu: normal and Umklapp parts against the oracle's split (same reading of Q, implemented
+    separately on each side), counts as integers; nu_select on fp_rates4 gives the same parts."""
+    cr = maker()
+    w, e, v = oracle_modes(cr)
+    temps = [300.0, 700.0]
+    with lib.Context.from_crystal(cr) as ctx:
+        ctx.set_modes(w, e, v)
+        nu, st = ctx.rates4_nu(temps, cr.scalebroad)
+        nu_m, _ = ctx.rates4_nu(temps, cr.scalebroad, precision=FP_PREC_MIXED)
+        umk, st_u = ctx.rates4(temps, cr.scalebroad, nu_select=2, no_graph=1)
+        with pytest.raises(lib.FourPhononError):
+            ctx.rates4(temps, cr.scalebroad, nu_select=3)
+        with pytest.raises(lib.FourPhononError):
+            ctx.rates4_nu(temps, cr.scalebroad, nu_select=1)
+    assert nu.shape == (len(temps), 2, cr.nq, cr.nb)
+    total = np.zeros(3)
+    for k, part in enumerate(("normal", "umklapp")):
+        ref, acc = oracle.rates4(cr, w, e, v, temps=temps, nu=part)
+        compare(nu[:, k].reshape(len(temps), -1), ref, RTOL_FP64)
+        compare(nu_m[:, k].reshape(len(temps), -1), ref, RTOL_MIXED)
+        total += acc
+    assert np.array_equal(np.array(st["accepted"]), total)
+    assert np.array_equal(umk, nu[:, 1])
