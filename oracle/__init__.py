@@ -48,7 +48,16 @@ def lib():
         L.oracle_rates4.argtypes = [ip, dp, ctypes.c_int, dp, ctypes.c_int, ip, dp, dp, dp, dp,
                                     ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_int, ctypes.c_int, ip, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                    dp, dp]
+                                    ctypes.c_int, dp, dp]
+        L.oracle_rates3.restype = ctypes.c_int
+        L.oracle_rates3.argtypes = [ip, dp, ctypes.c_int, dp, ctypes.c_int, ip, dp, dp, dp, dp, ctypes.c_int, dp,
+                                    ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int, ip,
+                                    ctypes.c_int, ctypes.c_int, dp, dp]
+        L.oracle_v3.restype = ctypes.c_int
+        L.oracle_v3.argtypes = [ip, dp, ctypes.c_int, dp, ctypes.c_int, ip, dp, dp, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int)]
+        L.oracle_umklapp.restype = ctypes.c_int
+        L.oracle_umklapp.argtypes = [ip, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.oracle_v4.restype = ctypes.c_int
         L.oracle_v4.argtypes = [ip, dp, ctypes.c_int, dp, ctypes.c_int, ip, dp, dp, ctypes.c_int,
                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, ip]
@@ -79,11 +88,13 @@ def evec_to_array(ev):
 
 
 def rates4(cryst, omega, evec, vel, temps=None, scalebroad=None, window=2.0, sigma_min=1e-10, dq_mode=0,
-           sel=None, unit_vertex=False, nthreads=0, processes=(0, 1, 2)):
+           sel=None, unit_vertex=False, nthreads=0, processes=(0, 1, 2), nu=None):
     """Rates (nT, nsel) in ps^-1 and accepted counts (3,) for modes sel (default: all).
 
     processes: the classes of Eq. 4phgamma summed, 0 ++ (recombination), 1 +- (redistribution), 2 --
-    (splitting); the default sums all three (the full rate)."""
+    (splitting); the default sums all three (the full rate).  nu: None (all), "normal" or "umklapp" (Sec. 2.2,
+    Q = 0 or not; the reading is in fp_oracle.c at orc_bz_shift)."""
+    nu_select = {None: 0, "normal": 1, "umklapp": 2}[nu]
     temps = cryst.temps if temps is None else temps
     sb = cryst.scalebroad if scalebroad is None else scalebroad
     nb = cryst.nb
@@ -108,7 +119,7 @@ def rates4(cryst, omega, evec, vel, temps=None, scalebroad=None, window=2.0, sig
     rc = lib().oracle_rates4(grid_p, lat_p, cryst.natoms, m_p, len(qi), qi_p, qf_p, om_p, ev_p, ve_p,
                              len(T), T_p, float(sb), float(window), float(sigma_min), int(dq_mode),
                              len(sel_a), sel_p, int(bool(unit_vertex)), sum(1 << int(p) for p in set(processes)),
-                             int(nthreads), out_p, acc_p)
+                             nu_select, int(nthreads), out_p, acc_p)
     if rc != 0:
         raise ValueError("oracle_rates4 rejected its arguments")
     return out, acc
@@ -161,3 +172,60 @@ def bose(w, T):
 
 def prefactor(nq):
     return lib().oracle_prefactor(int(nq))
+
+
+def umklapp(cryst, q, q1, q2, process):
+    """1 if process (0 ++, 1 +-, 2 --) with partners q1, q2 of mode wavevector q is Umklapp, 0 if normal."""
+    grid, grid_p = _i(np.asarray(cryst.grid))
+    lat, lat_p = _d(cryst.lattice)
+    r = lib().oracle_umklapp(grid_p, lat_p, int(q), int(q1), int(q2), int(process))
+    if r < 0:
+        raise ValueError("oracle_umklapp rejected its arguments")
+    return r
+
+
+def rates3(cryst, omega, evec, vel, temps=None, scalebroad=None, window=2.0, sigma_min=1e-10, dq_mode=0, sel=None,
+           unit_vertex=False, nthreads=0):
+    """Three-phonon RTA rates (nT, nsel) in ps^-1 (Eqs. tao0, 3phgamma, V3) and accepted counts (+, -)."""
+    temps = cryst.temps if temps is None else temps
+    sb = cryst.scalebroad if scalebroad is None else scalebroad
+    nb, N = cryst.nb, cryst.nq
+    if sel is None:
+        sel = np.arange(N * nb)
+    sel_a, sel_p = _i(np.asarray(sel))
+    grid, grid_p = _i(np.asarray(cryst.grid))
+    lat, lat_p = _d(cryst.lattice)
+    m, m_p = _d(cryst.mass)
+    qi, qi_p = _i(cryst.fc3_idx)
+    qf, qf_p = _d(cryst.fc3_val)
+    om_, om_p = _d(omega)
+    ev, ev_p = _d(evec_to_array(evec) if np.iscomplexobj(evec) else evec)
+    ve, ve_p = _d(vel)
+    T, T_p = _d(np.asarray(temps, float))
+    out = np.zeros((len(temps), len(sel_a)))
+    acc = np.zeros(2)
+    rc = lib().oracle_rates3(grid_p, lat_p, cryst.natoms, m_p, len(qi), qi_p, qf_p, om_p, ev_p, ve_p, len(T), T_p,
+                             float(sb), float(window), float(sigma_min), int(dq_mode), len(sel_a), sel_p,
+                             int(bool(unit_vertex)), int(nthreads), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                             acc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if rc != 0:
+        raise ValueError("oracle_rates3 rejected its arguments")
+    return out, acc
+
+
+def v3(cryst, evec, q, q1, process):
+    """Branch tensor V[j, j1, j2] (complex) of process 0 (+) or 1 (-) with partner q1, and q''."""
+    nb = cryst.nb
+    grid, grid_p = _i(np.asarray(cryst.grid))
+    lat, lat_p = _d(cryst.lattice)
+    m, m_p = _d(cryst.mass)
+    qi, qi_p = _i(cryst.fc3_idx)
+    qf, qf_p = _d(cryst.fc3_val)
+    ev, ev_p = _d(evec_to_array(evec) if np.iscomplexobj(evec) else evec)
+    out = np.zeros((nb, nb, nb, 2))
+    q2 = ctypes.c_int(0)
+    rc = lib().oracle_v3(grid_p, lat_p, cryst.natoms, m_p, len(qi), qi_p, qf_p, ev_p, int(q), int(q1), int(process),
+                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(q2))
+    if rc != 0:
+        raise ValueError("oracle_v3 rejected its arguments")
+    return out[..., 0] + 1j * out[..., 1], q2.value

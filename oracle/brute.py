@@ -71,3 +71,38 @@ def vertex(cryst, P, evec, q, q1, q2, q3, conj1=False, conj2=False):
     if conj2:
         u2 = u2.conj()
     return np.einsum("IJKL,Ia,Jb,Kc,Ld->abcd", P, u0, u1, u2, u3.conj(), optimize=True) / N
+
+
+def supercell_phi3(cryst):
+    """Third-order force constants folded onto the Born-von Karman supercell (for Eq. V3)."""
+    grid = cryst.grid
+    N = int(np.prod(grid))
+    nat = cryst.natoms
+    n = 3 * nat * N
+    P = np.zeros((n, n, n))
+    cells = list(itertools.product(range(grid[0]), range(grid[1]), range(grid[2])))
+
+    def site(c, R, atom):
+        cc = [(c[a] + int(R[a])) % grid[a] for a in range(3)]
+        ci = (cc[0] * grid[1] + cc[1]) * grid[2] + cc[2]
+        return 3 * (ci * nat + atom)
+
+    for idx, val in zip(cryst.fc3_idx, cryst.fc3_val):
+        i, j, k = (int(x) for x in idx[:3])
+        Rj, Rk = idx[3:6], idx[6:9]
+        blk = val.reshape(3, 3, 3)
+        for c in cells:
+            P[site(c, (0, 0, 0), i):site(c, (0, 0, 0), i) + 3, site(c, Rj, j):site(c, Rj, j) + 3,
+              site(c, Rk, k):site(c, Rk, k) + 3] += blk
+    return P
+
+
+def vertex3(cryst, P3, evec, q, q1, q2, conj1=False):
+    """V[j, j1, j2] = (1/N) sum Phi3_sc u_q u_q1 conj(u_q2); conj1 gives the e^{-lambda'} leg."""
+    N = int(np.prod(cryst.grid))
+    u0 = displacement(cryst, q, evec[q])
+    u1 = displacement(cryst, q1, evec[q1])
+    u2 = displacement(cryst, q2, evec[q2])
+    if conj1:
+        u1 = u1.conj()
+    return np.einsum("IJK,Ia,Jb,Kc->abc", P3, u0, u1, u2.conj(), optimize=True) / N

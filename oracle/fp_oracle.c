@@ -128,6 +128,57 @@ static cplx orc_e(const orc_problem* p, int q, int branch, int comp) {
 
 static double orc_bose(double w, double T) { return 1.0 / expm1(ORC_HBAR * w / (ORC_KB * T)); }
 
+/*
+ * Normal / Umklapp (Sec. 2.2: q''' = q + s1 q' + s2 q'' + Q, with Q = 0 for a normal process).  Reading:
+ * each grid wavevector is taken as its shortest translate k = sum_a (g_a / N_a - m_a) b_a over integers m_a in
+ * [-2, 2]; squared lengths within 1e-9 relative of each other are a tie, won by the lexicographically
+ * smallest m.  The process is normal when these representatives satisfy q + s1 q' + s2 q'' - q''' = 0.
+ */
+static void orc_bz_shift(const orc_problem* p, int q, int m[3]) {
+  int g[3];
+  orc_unidx(p, q, g);
+  double best = -1.0;
+  for (int m0 = -2; m0 <= 2; ++m0)
+    for (int m1 = -2; m1 <= 2; ++m1)
+      for (int m2 = -2; m2 <= 2; ++m2) {
+        const int mm[3] = {m0, m1, m2};
+        double k2 = 0.0;
+        for (int c = 0; c < 3; ++c) {
+          double kc = 0.0;
+          for (int a = 0; a < 3; ++a) kc += ((double)g[a] / (double)p->grid[a] - (double)mm[a]) * p->rec[3 * a + c];
+          k2 += kc * kc;
+        }
+        /* the loops run in lexicographic order of m, so a tie keeps the earlier (smaller) m */
+        if (best < 0.0 || k2 < best * (1.0 - 1e-9)) {
+          best = k2;
+          m[0] = m0;
+          m[1] = m1;
+          m[2] = m2;
+        }
+      }
+}
+
+/* 1 if process (s1, s2) with partners q1, q2 (q3 = q + s1 q1 + s2 q2 on the grid) is Umklapp, else 0;
+   shift: nq x 3, orc_bz_shift of every grid point */
+static int orc_is_umklapp(const orc_problem* p, const int* shift, int q, int q1, int q2, int s1, int s2) {
+  int g[3], g1[3], g2[3], g3[3];
+  orc_unidx(p, q, g);
+  orc_unidx(p, q1, g1);
+  orc_unidx(p, q2, g2);
+  for (int a = 0; a < 3; ++a) g3[a] = orc_wrap(g[a] + s1 * g1[a] + s2 * g2[a], p->grid[a]);
+  const int* m = shift + 3 * q;
+  const int* m1 = shift + 3 * q1;
+  const int* m2 = shift + 3 * q2;
+  const int* m3 = shift + 3 * orc_idx(p, g3);
+  for (int a = 0; a < 3; ++a) {
+    /* N_a times the a-th reduced coordinate of q + s1 q1 + s2 q2 - q3, taken in the representatives */
+    const int n = p->grid[a];
+    const int num = (g[a] - n * m[a]) + s1 * (g1[a] - n * m1[a]) + s2 * (g2[a] - n * m2[a]) - (g3[a] - n * m3[a]);
+    if (num != 0) return 1;
+  }
+  return 0;
+}
+
 /* Third wavevector of process (s1, s2): q''' = q + s1 q' + s2 q'' on the grid. */
 static int orc_third(const orc_problem* p, int q, int q1, int q2, int s1, int s2) {
   int g[3], g1[3], g2[3], g3[3];
@@ -231,14 +282,16 @@ static const double ORC_MULT[3] = {0.5, 0.5, 1.0 / 6.0};
  *   unit_vertex != 0 replaces |V|^2 by 1 (the weighted phase space of the same processes).
  *   proc_mask selects the process classes summed in Eq. 4phgamma: bit 0 ++ (recombination), bit 1 +-
  *   (redistribution), bit 2 -- (splitting); 7 gives the full rate.
+ *   nu_select: 0 all processes, 1 normal ones only, 2 Umklapp ones only (orc_is_umklapp).
  * Returns 0, or -1 on bad arguments.
  */
 int oracle_rates4(const int grid[3], const double lattice[9], int natoms, const double* mass, int nquart,
                   const int* qidx, const double* qfc, const double* omega, const double* evec,
                   const double* vel, int nT, const double* T, double scalebroad, double window,
                   double sigma_min, int dq_mode, int nsel, const int* sel, int unit_vertex, int proc_mask,
-                  int nthreads, double* rates, double* accepted) {
+                  int nu_select, int nthreads, double* rates, double* accepted) {
   if (!grid || !lattice || natoms <= 0 || nT <= 0 || nsel < 0 || proc_mask < 0 || proc_mask > 7) return -1;
+  if (nu_select < 0 || nu_select > 2) return -1;
   orc_problem P;
   orc_setup(&P, grid, lattice, natoms, mass, nquart, qidx, qfc, omega, evec, vel);
   const int nb = P.nb, nq = P.nq;
@@ -248,6 +301,8 @@ int oracle_rates4(const int grid[3], const double lattice[9], int natoms, const 
   const double pref = M_PI * ORC_HBAR * ORC_HBAR * conv * conv * conv * conv / (8.0 * (double)nq * (double)nq);
   for (int k = 0; k < 3; ++k) accepted[k] = 0.0;
   memset(rates, 0, sizeof(double) * (size_t)nT * nsel);
+  int* shift = (int*)malloc(sizeof(int) * 3 * (size_t)nq);
+  for (int k = 0; k < nq; ++k) orc_bz_shift(&P, k, shift + 3 * k);
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #endif
@@ -268,6 +323,10 @@ int oracle_rates4(const int grid[3], const double lattice[9], int natoms, const 
             if (!((proc_mask >> pr) & 1)) continue;
             const int s1 = ORC_S1[pr], s2 = ORC_S2[pr];
             const int q3 = orc_third(&P, q, q1, q2, s1, s2);
+            if (nu_select != 0) {
+              const int u = orc_is_umklapp(&P, shift, q, q1, q2, s1, s2);
+              if ((nu_select == 1) == (u != 0)) continue;
+            }
             int have_phi = 0;
             for (int j1 = 0; j1 < nb; ++j1) {
               const double w1 = omega[q1 * nb + j1];
@@ -330,7 +389,24 @@ int oracle_rates4(const int grid[3], const double lattice[9], int natoms, const 
     free(part);
     free(cnt);
   }
+  free(shift);
   return 0;
+}
+
+/*
+ * Normal (0) or Umklapp (1) classification of process pr (0 ++, 1 +-, 2 --) with explicit partners q1, q2
+ * (orc_is_umklapp); -1 on bad arguments.  Exposed so that tests can check hand-worked cases.
+ */
+int oracle_umklapp(const int grid[3], const double lattice[9], int q, int q1, int q2, int pr) {
+  if (!grid || !lattice || pr < 0 || pr > 2) return -1;
+  orc_problem P;
+  orc_setup(&P, grid, lattice, 1, NULL, 0, NULL, NULL, NULL, NULL, NULL);
+  if (q < 0 || q1 < 0 || q2 < 0 || q >= P.nq || q1 >= P.nq || q2 >= P.nq) return -1;
+  int* shift = (int*)malloc(sizeof(int) * 3 * (size_t)P.nq);
+  for (int k = 0; k < P.nq; ++k) orc_bz_shift(&P, k, shift + 3 * k);
+  const int u = orc_is_umklapp(&P, shift, q, q1, q2, ORC_S1[pr], ORC_S2[pr]);
+  free(shift);
+  return u;
 }
 
 /*
@@ -431,6 +507,172 @@ int oracle_phase3(const int grid[3], const double lattice[9], int natoms, const 
     }
     p3[s] = acc_p / (double)nq;
     for (int it = 0; it < nT && it < 64; ++it) wp3[(size_t)it * nsel + s] = acc_w[it] / (double)nq;
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------------------------
+ * Three-phonon rates (Eqs. tao0, 3phgamma, V3), the same conventions as the four-phonon part:
+ *   1/tau3_l = (1/N) [ sum_{l' l''}^{(+)} G+ + 1/2 sum_{l' l''}^{(-)} G- ],
+ *   G+- = (hbar pi / 4) B+- / (w w' w'') |V+-|^2 delta(w +- w' - w''),  B+ = n' - n'',  B- = n' + n'' + 1,
+ *   q'' = q +- q' on the grid,
+ *   V+- = sum_{ijk} sum_{abg} Phi3 e_a(l)(i) e_b(+-l')(j) e_g(-l'')(k) / sqrt(Mi Mj Mk) exp(+-i q'.r_j) exp(-i q''.r_k),
+ * with e(-l) = conj e(l).  sigma = sb |v' - v''| dq at the actual q', q'' (the adaptive broadening of
+ * Sec. 2.4 applied to the two partner modes); the window and delta follow the four-phonon rules.
+ * |V|^2 in eV^2/(A^6 amu^3) = conv^3 ps^-6 / eV, so the prefactor is (pi/4) hbar conv^3 / N.
+ * ------------------------------------------------------------------------------------------------------ */
+static void orc_phi3(const orc_problem* p, int n3, const int* idx3, const double* fc3, int q1, int q2, int s1,
+                     cplx* phi) {
+  const int nb = p->nb;
+  double k1[3], k2[3];
+  orc_qcart(p, q1, k1);
+  orc_qcart(p, q2, k2);
+  memset(phi, 0, sizeof(cplx) * (size_t)nb * nb * nb);
+  for (int Q = 0; Q < n3; ++Q) {
+    const int* ix = idx3 + 9 * Q;
+    double rj[3], rk[3];
+    orc_rcart(p, ix + 3, rj);
+    orc_rcart(p, ix + 6, rk);
+    double ang = 0.0;
+    for (int c = 0; c < 3; ++c) ang += s1 * k1[c] * rj[c] - k2[c] * rk[c];
+    cplx ph = cos(ang) + I * sin(ang);
+    double msq = sqrt(p->mass[ix[0]] * p->mass[ix[1]] * p->mass[ix[2]]);
+    const double* fc = fc3 + 27 * Q;
+    for (int al = 0; al < 3; ++al)
+      for (int be = 0; be < 3; ++be)
+        for (int ga = 0; ga < 3; ++ga) {
+          int a = 3 * ix[0] + al, b = 3 * ix[1] + be, c = 3 * ix[2] + ga;
+          phi[(a * nb + b) * nb + c] += fc[(al * 3 + be) * 3 + ga] / msq * ph;
+        }
+  }
+}
+
+static cplx orc_vertex3(const orc_problem* p, const cplx* phi, int q, int j, int q1, int j1, int q2, int j2,
+                        int s1) {
+  const int nb = p->nb;
+  cplx acc = 0.0;
+  for (int a = 0; a < nb; ++a) {
+    cplx ea = orc_e(p, q, j, a);
+    for (int b = 0; b < nb; ++b) {
+      cplx eb = orc_e(p, q1, j1, b);
+      if (s1 < 0) eb = conj(eb);
+      for (int c = 0; c < nb; ++c) acc += phi[(a * nb + b) * nb + c] * ea * eb * conj(orc_e(p, q2, j2, c));
+    }
+  }
+  return acc;
+}
+
+/* V+- tensor out[((j nb + j1) nb + j2)] (re, im) of process 0 (+) or 1 (-) with partner q1; *q2_out = q'' */
+int oracle_v3(const int grid[3], const double lattice[9], int natoms, const double* mass, int n3, const int* idx3,
+              const double* fc3, const double* evec, int q, int q1, int process, double* out, int* q2_out) {
+  if (!grid || !lattice || natoms <= 0 || process < 0 || process > 1) return -1;
+  orc_problem P;
+  orc_setup(&P, grid, lattice, natoms, mass, 0, NULL, NULL, NULL, evec, NULL);
+  const int nb = P.nb, s1 = process == 0 ? 1 : -1;
+  if (q < 0 || q1 < 0 || q >= P.nq || q1 >= P.nq) return -1;
+  int g[3], g1[3], g2[3];
+  orc_unidx(&P, q, g);
+  orc_unidx(&P, q1, g1);
+  for (int a = 0; a < 3; ++a) g2[a] = orc_wrap(g[a] + s1 * g1[a], grid[a]);
+  const int q2 = orc_idx(&P, g2);
+  cplx* phi = (cplx*)malloc(sizeof(cplx) * (size_t)nb * nb * nb);
+  orc_phi3(&P, n3, idx3, fc3, q1, q2, s1, phi);
+  for (int j = 0; j < nb; ++j)
+    for (int j1 = 0; j1 < nb; ++j1)
+      for (int j2 = 0; j2 < nb; ++j2) {
+        cplx V = orc_vertex3(&P, phi, q, j, q1, j1, q2, j2, s1);
+        out[2 * ((j * nb + j1) * nb + j2)] = creal(V);
+        out[2 * ((j * nb + j1) * nb + j2) + 1] = cimag(V);
+      }
+  free(phi);
+  *q2_out = q2;
+  return 0;
+}
+
+/*
+ * Three-phonon RTA rates of selected modes: rates[t * nsel + s] in ps^-1; accepted[2]: terms inside the
+ * window, + and - processes.  unit_vertex != 0 replaces |V|^2 by 1 (then the sum, without the prefactor, is
+ * the weighted phase space WP3 of oracle_phase3).
+ */
+int oracle_rates3(const int grid[3], const double lattice[9], int natoms, const double* mass, int n3,
+                  const int* idx3, const double* fc3, const double* omega, const double* evec, const double* vel,
+                  int nT, const double* T, double scalebroad, double window, double sigma_min, int dq_mode, int nsel,
+                  const int* sel, int unit_vertex, int nthreads, double* rates, double* accepted) {
+  if (!grid || !lattice || natoms <= 0 || nT <= 0 || nsel < 0) return -1;
+  orc_problem P;
+  orc_setup(&P, grid, lattice, natoms, mass, 0, NULL, NULL, omega, evec, vel);
+  const int nb = P.nb, nq = P.nq;
+  const double dq = orc_dq_iso(&P);
+  const double conv = orc_conv();
+  const double pref = M_PI * ORC_HBAR * conv * conv * conv / (4.0 * (double)nq);
+  accepted[0] = accepted[1] = 0.0;
+  memset(rates, 0, sizeof(double) * (size_t)nT * nsel);
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+  for (int s = 0; s < nsel; ++s) {
+    const int q = sel[s] / nb, j = sel[s] % nb;
+    const double w = omega[sel[s]];
+    if (w == 0.0) continue;
+    double* part = (double*)calloc((size_t)nq * nT, sizeof(double));
+    double* cnt = (double*)calloc((size_t)nq * 2, sizeof(double));
+#pragma omp parallel
+    {
+      cplx* phi = (cplx*)malloc(sizeof(cplx) * (size_t)nb * nb * nb);
+#pragma omp for schedule(dynamic, 1)
+      for (int q1 = 0; q1 < nq; ++q1) {
+        for (int pr = 0; pr < 2; ++pr) {
+          const int s1 = pr == 0 ? 1 : -1;
+          int g[3], g1[3], g2[3];
+          orc_unidx(&P, q, g);
+          orc_unidx(&P, q1, g1);
+          for (int a = 0; a < 3; ++a) g2[a] = orc_wrap(g[a] + s1 * g1[a], grid[a]);
+          const int q2 = orc_idx(&P, g2);
+          int have_phi = 0;
+          for (int j1 = 0; j1 < nb; ++j1) {
+            const double w1 = omega[q1 * nb + j1];
+            if (w1 == 0.0) continue;
+            for (int j2 = 0; j2 < nb; ++j2) {
+              const double w2 = omega[q2 * nb + j2];
+              if (w2 == 0.0) continue;
+              const double dw = ((s1 > 0) ? (w + w1) : (w - w1)) - w2;
+              const double sigma =
+                  orc_sigma(&P, vel + 3 * (q1 * nb + j1), vel + 3 * (q2 * nb + j2), scalebroad, dq, dq_mode);
+              const double sw = (sigma < sigma_min) ? sigma_min : sigma;
+              if (!(fabs(dw) <= window * sw)) continue;
+              const double delta =
+                  (sigma < sigma_min) ? 1.0 : exp(-(dw * dw) / (sigma * sigma)) / (sqrt(M_PI) * sigma);
+              double v2 = 1.0;
+              if (!unit_vertex) {
+                if (!have_phi) {
+                  orc_phi3(&P, n3, idx3, fc3, q1, q2, s1, phi);
+                  have_phi = 1;
+                }
+                cplx V = orc_vertex3(&P, phi, q, j, q1, j1, q2, j2, s1);
+                v2 = creal(V) * creal(V) + cimag(V) * cimag(V);
+              }
+              cnt[2 * q1 + pr] += 1.0;
+              for (int it = 0; it < nT; ++it) {
+                const double n1 = orc_bose(w1, T[it]);
+                const double n2 = orc_bose(w2, T[it]);
+                const double B = (pr == 0) ? (n1 - n2) : (n1 + n2 + 1.0);
+                const double mult = (pr == 0) ? 1.0 : 0.5;
+                part[(size_t)q1 * nT + it] += mult * B * v2 * delta / (w * w1 * w2);
+              }
+            }
+          }
+        }
+      }
+      free(phi);
+    }
+    for (int q1 = 0; q1 < nq; ++q1) {
+      for (int it = 0; it < nT; ++it) rates[(size_t)it * nsel + s] += part[(size_t)q1 * nT + it];
+      accepted[0] += cnt[2 * q1];
+      accepted[1] += cnt[2 * q1 + 1];
+    }
+    for (int it = 0; it < nT; ++it) rates[(size_t)it * nsel + s] *= unit_vertex ? 1.0 / (double)nq : pref;
+    free(part);
+    free(cnt);
   }
   return 0;
 }

@@ -48,6 +48,8 @@ class Crystal:
     temps: tuple = (300.0,)
     scalebroad: float = 1.0
     extra: dict = field(default_factory=dict)
+    fc3_idx: np.ndarray = None   # (n3,9) int32: i, j, k, Rj[3], Rk[3]
+    fc3_val: np.ndarray = None   # (n3,27) float64, eV/A^3, row-major alpha,beta,gamma
 
     @property
     def natoms(self) -> int:
@@ -64,7 +66,8 @@ class Crystal:
     def with_grid(self, grid, temps=None) -> "Crystal":
         c = Crystal(self.name, self.lattice, self.frac, self.mass, self.fc2_idx, self.fc2_val,
                     self.fc4_idx, self.fc4_val, tuple(int(g) for g in grid),
-                    tuple(temps) if temps is not None else self.temps, self.scalebroad, dict(self.extra))
+                    tuple(temps) if temps is not None else self.temps, self.scalebroad, dict(self.extra),
+                    self.fc3_idx, self.fc3_val)
         return c
 
     def scaled_fc4(self, s: float) -> "Crystal":
@@ -156,6 +159,37 @@ def _fc4_from_bonds(bonds, tensors):
     return idx, val
 
 
+def _fc3_from_bonds(bonds, tensors):
+    """Triplet list from third-order bond tensors: sites {a@0, b@R}^3 with the sign product of the bond's ends
+    (-1 at a, +1 at b: the derivatives of K (u_b - u_a)^3 / 6), shifted so the first atom is in cell 0. Each
+    index sums to zero over the other two (acoustic sum rule) by construction."""
+    acc = {}
+    for (a, b, R, _d), K in zip(bonds, tensors):
+        sites = [(a, (0, 0, 0), -1.0), (b, tuple(R), +1.0)]
+        for combo in itertools.product(sites, repeat=3):
+            sgn = combo[0][2] * combo[1][2] * combo[2][2]
+            c0 = np.asarray(combo[0][1])
+            atoms = tuple(s[0] for s in combo)
+            cells = tuple(tuple(int(v) for v in (np.asarray(s[1]) - c0)) for s in combo[1:])
+            key = (atoms, cells)
+            acc[key] = acc.get(key, np.zeros((3, 3, 3))) + sgn * K
+    keys = sorted(acc)
+    idx = np.array([[*k[0], *k[1][0], *k[1][1]] for k in keys], dtype=np.int32)
+    val = np.array([acc[k].reshape(27) for k in keys], dtype=np.float64)
+    return idx, val
+
+
+def _draw_fc3(bonds, seed_index, scale=5.0):
+    """Seeded third-order bond tensors, N(0, scale eV/A^3) entrywise, averaged over index permutations; drawn
+    from their own stream so that the fourth-order draws do not change."""
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + 1000 + seed_index))
+    out = []
+    for _ in bonds:
+        K = rng.normal(0.0, scale, size=(3, 3, 3))
+        out.append(sum(np.transpose(K, p) for p in itertools.permutations(range(3))) / 6.0)
+    return _fc3_from_bonds(bonds, out)
+
+
 def _draw_tensors(rng, n, scale=5.0):
     return [_sym24(rng.normal(0.0, scale, size=(3, 3, 3, 3))) for _ in range(n)]
 
@@ -214,8 +248,9 @@ def simple_cubic(grid=(4, 4, 4), seed_index=1, symmetric=False, temps=(300.0,), 
         K = _point_group_tensors([b[3] for b in bonds], K, _signed_perms())
         extra["point_group"] = _signed_perms()
     i4, v4 = _fc4_from_bonds(bonds, K)
+    i3, v3 = _draw_fc3(bonds, seed_index)
     return Crystal("simple-cubic" + ("-sym" if symmetric else ""), lattice, frac, mass, i2, v2, i4, v4,
-                   tuple(grid), tuple(temps), scalebroad, extra)
+                   tuple(grid), tuple(temps), scalebroad, extra, i3, v3)
 
 
 def _fcc_two_atom(a, masses, name, grid, seed_index, symmetric, temps, scalebroad):
@@ -238,8 +273,9 @@ def _fcc_two_atom(a, masses, name, grid, seed_index, symmetric, temps, scalebroa
         K = _point_group_tensors(vecs, K, ops)
         extra["point_group"] = ops
     i4, v4 = _fc4_from_bonds(bonds, K)
+    i3, v3 = _draw_fc3(bonds, seed_index)
     return Crystal(name + ("-sym" if symmetric else ""), lattice, frac, mass, i2, v2, i4, v4,
-                   tuple(grid), tuple(temps), scalebroad, extra)
+                   tuple(grid), tuple(temps), scalebroad, extra, i3, v3)
 
 
 def diamond_si(grid=(8, 8, 8), seed_index=2, symmetric=False, temps=(300.0,), scalebroad=1.0):
@@ -296,7 +332,8 @@ def licoo2(grid=(10, 10, 6), seed_index=4, temps=(300.0, 500.0, 700.0), scalebro
     rng = np.random.Generator(np.random.PCG64(SEED_BASE + seed_index))
     K = _draw_tensors(rng, len(bonds))
     i4, v4 = _fc4_from_bonds(bonds, K)
-    return Crystal("licoo2", lattice, frac, mass, i2, v2, i4, v4, tuple(grid), tuple(temps), scalebroad)
+    i3, v3 = _draw_fc3(bonds, seed_index)
+    return Crystal("licoo2", lattice, frac, mass, i2, v2, i4, v4, tuple(grid), tuple(temps), scalebroad, {}, i3, v3)
 
 
 TEMPS_SWEEP = tuple(float(t) for t in range(300, 1001, 100))

@@ -197,3 +197,52 @@ def test_process_classes_split_the_rate():
     np.testing.assert_allclose(parts[0] + parts[1] + parts[2], full, rtol=1e-13, atol=0.0)
     two, _ = oracle.rates4(cr, w, e, v, sel=sel, temps=temps, processes=(0, 2))
     np.testing.assert_allclose(two, parts[0] + parts[2], rtol=1e-13, atol=0.0)
+
+
+def test_umklapp_hand_worked_cases():
+    """Normal/Umklapp (Sec. 2.2: q''' = q + s1 q' + s2 q'' + Q, Q = 0 normal) with each wavevector taken as its
+    shortest translate, ties to the smallest shift. Cases worked by hand on simple-cubic grids."""
+    idx = lambda g, n: (g[0] * n + g[1]) * n + g[2]
+    cr3 = synth.simple_cubic((3, 3, 3))  # representatives 0, 1/3, -1/3 (no ties)
+    x1, x2, G = idx((1, 0, 0), 3), idx((2, 0, 0), 3), 0
+    # ++: 1/3 + 1/3 + 1/3 = 1 -> q''' = Gamma, Q = 1: Umklapp
+    assert oracle.umklapp(cr3, x1, x1, x1, 0) == 1
+    # ++: 1/3 + 1/3 + 0 = 2/3 ~ -1/3: Umklapp
+    assert oracle.umklapp(cr3, x1, x1, G, 0) == 1
+    # ++: 1/3 + (-1/3) + 0 = 0: normal
+    assert oracle.umklapp(cr3, x1, x2, G, 0) == 0
+    # +-: 1/3 + 1/3 - 1/3 = 1/3: normal
+    assert oracle.umklapp(cr3, x1, x1, x1, 1) == 0
+    # --: 1/3 - (-1/3) - (-1/3) = 1 ~ 0: Umklapp
+    assert oracle.umklapp(cr3, x1, x2, x2, 2) == 1
+    # --: 1/3 - 1/3 - 0 = 0: normal
+    assert oracle.umklapp(cr3, x1, x1, G, 2) == 0
+    cr2 = synth.simple_cubic((2, 2, 2))  # 1/2 and -1/2 tie: the representative is +1/2
+    y = idx((1, 0, 0), 2)
+    assert oracle.umklapp(cr2, y, y, y, 0) == 1      # 3/2 - 1/2 = 1
+    assert oracle.umklapp(cr2, y, y, y, 1) == 0      # 1/2 + 1/2 - 1/2 - 1/2 = 0
+    assert oracle.umklapp(cr2, G, G, y, 0) == 0      # 0 + 0 + 1/2 - 1/2 = 0
+    d = idx((1, 1, 0), 2)                            # (1/2, 1/2, 0): four tied translates, (+1/2, +1/2, 0) wins
+    assert oracle.umklapp(cr2, d, y, G, 1) == 1      # (1/2, 1/2, 0) + (1/2, 0, 0) - 0 - (0, 1/2, 0) = (1, 0, 0)
+    assert oracle.umklapp(cr2, d, G, G, 1) == 0      # q''' = q
+
+
+def test_normal_and_umklapp_split_the_rate():
+    """The normal and Umklapp parts add up to the full rate, per process class, with the counts split alike;
+    on a 1 x 1 x 1 grid every wavevector is Gamma and every process is normal."""
+    cr = synth.diamond_si((3, 3, 2))
+    w, e, v = oracle_modes(cr)
+    nb = cr.nb
+    sel = [nb * 1 + 2, nb * 7 + 4, nb * 12 + 5]
+    full, acc = oracle.rates4(cr, w, e, v, sel=sel)
+    rn, an = oracle.rates4(cr, w, e, v, sel=sel, nu="normal")
+    ru, au = oracle.rates4(cr, w, e, v, sel=sel, nu="umklapp")
+    assert np.array_equal(an + au, acc) and an[1] > 0 and au[1] > 0
+    np.testing.assert_allclose(rn + ru, full, rtol=1e-13, atol=0.0)
+    one = synth.diamond_si((1, 1, 1))
+    w1, e1, v1 = oracle_modes(one)
+    f1, a1 = oracle.rates4(one, w1, e1, v1)
+    n1, b1 = oracle.rates4(one, w1, e1, v1, nu="normal")
+    u1, c1 = oracle.rates4(one, w1, e1, v1, nu="umklapp")
+    assert np.array_equal(n1, f1) and np.array_equal(b1, a1)
+    assert np.all(u1 == 0.0) and np.all(c1 == 0.0)

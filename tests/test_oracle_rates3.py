@@ -1,0 +1,79 @@
+"""Pins of the oracle's three-phonon rates (Eqs. tao0, 3phgamma, V3).
+
+* brute force: the Born-von Karman supercell sum over every atom triplet equals Eq. V3 on tiny grids, for
+  both processes (e^{-lambda'} = conj e(lambda'));
+* the vertex is symmetric under exchanging its last two legs with time reversal: V+(q, q', q'') equals
+  V-(q, -q', q'') for the same triple of modes;
+* |V|^2 := 1 turns the rate sum into the weighted three-phonon phase space that oracle.phase3 computes
+  independently; the rates are exactly quadratic in Phi3 and vanish with it.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import oracle.brute as brute
+import oracle.modes as om
+from paper_2104_04895_gb300 import synth
+from conftest import oracle_modes
+
+
+def idx_of(cr, g):
+    ng = np.array(cr.grid)
+    g = np.asarray(g) % ng
+    return int((g[0] * ng[1] + g[1]) * ng[2] + g[2])
+
+
+@pytest.mark.parametrize("maker", [lambda: synth.simple_cubic((2, 2, 2)), lambda: synth.simple_cubic((3, 2, 1)),
+                                   lambda: synth.diamond_si((2, 1, 1)), lambda: synth.zincblende_bas((2, 2, 1))])
+def test_vertex3_equals_supercell_brute_force(maker, rng):
+    cr = maker()
+    w, e, v = oracle_modes(cr)
+    P3 = brute.supercell_phi3(cr)
+    G = om.grid_points(cr.grid)
+    natural = np.abs(cr.fc3_val).sum() / cr.mass.min() ** 1.5
+    for trial in range(4):
+        q, q1 = (int(x) for x in rng.integers(0, cr.nq, size=2))
+        for pr, s1 in ((0, 1), (1, -1)):
+            V, q2 = oracle.v3(cr, e, q, q1, pr)
+            assert q2 == idx_of(cr, G[q] + s1 * G[q1])
+            Vb = brute.vertex3(cr, P3, e, q, q1, q2, conj1=s1 < 0)
+            scale = max(np.abs(Vb).max(), 1e-3 * natural)
+            assert np.abs(V - Vb).max() <= 1e-12 * scale, (q, q1, pr)
+
+
+def test_plus_and_minus_share_the_vertex():
+    """V-(q, q') with q'' = q - q' equals V+(q, -q') (same q''), since e(-q') = conj e(q')."""
+    cr = synth.diamond_si((3, 2, 2))
+    w, e, v = oracle_modes(cr)
+    G = om.grid_points(cr.grid)
+    for q, q1 in ((1, 5), (7, 3), (0, 11)):
+        Vm, q2m = oracle.v3(cr, e, q, q1, 1)
+        Vp, q2p = oracle.v3(cr, e, q, idx_of(cr, -G[q1]), 0)
+        assert q2m == q2p
+        np.testing.assert_allclose(Vm, Vp, rtol=0, atol=1e-12 * np.abs(Vp).max())
+
+
+def test_unit_vertex_is_the_weighted_phase_space():
+    cr = synth.diamond_si((3, 3, 2))
+    w, e, v = oracle_modes(cr)
+    temps = [300.0, 800.0]
+    sel = np.arange(cr.nb, cr.nq * cr.nb, 7)
+    r1, acc = oracle.rates3(cr, w, e, v, temps=temps, sel=sel, unit_vertex=True)
+    _, wp3 = oracle.phase3(cr, w, v, temps=temps, sel=sel)
+    np.testing.assert_allclose(r1, wp3, rtol=1e-12, atol=0.0)
+    assert acc[0] > 0 and acc[1] > 0
+
+
+def test_quadratic_in_phi3():
+    cr = synth.simple_cubic((3, 3, 3))
+    w, e, v = oracle_modes(cr)
+    sel = [5, 17, 40]
+    r, _ = oracle.rates3(cr, w, e, v, sel=sel)
+    c2 = cr.with_grid(cr.grid)
+    c2.fc3_val = 2.0 * cr.fc3_val
+    r2, _ = oracle.rates3(c2, w, e, v, sel=sel)
+    assert np.array_equal(r2, 4.0 * r)
+    c0 = cr.with_grid(cr.grid)
+    c0.fc3_val = 0.0 * cr.fc3_val
+    r0, _ = oracle.rates3(c0, w, e, v, sel=sel)
+    assert np.all(r0 == 0.0) and np.all(r > 0.0)
