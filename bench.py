@@ -268,6 +268,15 @@ def main():
                               "pipe": "fp64" if other_prec == binding.FP_PREC_FP64 else "fp32",
                               "kernel_ms": o_kms}}
 
+    # three-phonon rates of the same workload (FP64, one launch after a warm-up launch), for context
+    three = None
+    if not args.no_other and cr.fc3_idx is not None:
+        ctx.rates3(cr.temps, cr.scalebroad, q_begin=q0, q_end=q1)
+        _, st3 = ctx.rates3(cr.temps, cr.scalebroad, q_begin=q0, q_end=q1)
+        s3 = max_over_ranks(st3["ms"], dist if ws > 1 else None, dev) * 1e-3
+        three = {"precision": "fp64", "s_per_rate_set": s3, "candidates": st3["candidates"],
+                 "terms_per_s": st3["candidates"] / s3, "accepted": st3["accepted"][:2]}
+
     # end to end through the public API with host buffers
     e2e_times = []
     h2d = d2h = 0
@@ -318,6 +327,7 @@ def main():
                          "pipe": "fp64" if main_prec == binding.FP_PREC_FP64 else "fp32",
                          "kernel_ms": kms, "flops_per_launch": st["flops"]},
             "other_precision": other,
+            "three_phonon": three,
             "cpu_baseline": base,
             "e2e": {"value": e2e_value, "unit": "process-terms/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "s_per_rate_set": e2e_s},

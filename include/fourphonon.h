@@ -199,6 +199,41 @@ int fp_rates4_channels(fp_ctx* ctx, int nT, const double* T, double scalebroad, 
                        double* rates, fp_stats* stats);
 
 /*
+ * Third-order force constants for the three-phonon rates (Eq. V3): triplet (i, j, k) with atom i in the home
+ * cell and atoms j, k in cells Rj, Rk (lattice units); fc[(a*3 + b)*3 + g] in eV/A^3.
+ */
+typedef struct {
+  int i, j, k;
+  int Rj[3], Rk[3];
+  double fc[27];
+} fp_fc3;
+
+/* Store (replace) the third-order force constants of the context.  The library copies them. */
+int fp_set_fc3(fp_ctx* ctx, int n_fc3, const fp_fc3* fc3);
+
+/*
+ * Three-phonon RTA rates (Eqs. tao0, 3phgamma, V3): 1/tau3 = (1/N) [sum^(+) G+ + 1/2 sum^(-) G-] with
+ * G+- = (hbar pi / 4) B+- |V+-|^2 delta(w +- w' - w'') / (w w' w''), B+ = n' - n'', B- = n' + n'' + 1,
+ * q'' = q +- q'.  The broadening is sb |v' - v''| dq at the two partner modes (Sec. 2.4), with the window and
+ * sigma_min rules of fp_rates4.  FP64.  opts: window, sigma_min, dq_mode, mode_mask and the q range apply;
+ * the other fields are ignored.  rates: host, nT x N x nb, ps^-1 (add fp_rates4's rates for the total).
+ * stats: candidates 2 N nb^2 per selected mode, accepted[0] (+) and accepted[1] (-).  FP_ESTATE before
+ * fp_set_fc3 or the modes.
+ */
+int fp_rates3(fp_ctx* ctx, int nT, const double* T, double scalebroad, const fp_rates_opts* opts, double* rates,
+              fp_stats* stats);
+
+/*
+ * RTA lattice thermal conductivity from total rates (e.g. fp_rates3 + fp_rates4): kappa_ab(T) = k_B / (N V)
+ * sum_l c(x_l) v_a(l) v_b(l) / rate_l with c(x) = x^2 e^x / (e^x - 1)^2, x = hbar w / (k_B T), V the cell
+ * volume; modes with w = 0 or rate <= 0 are left out.  The paper's rates are the RTA input of this tensor
+ * (Sec. 2.1, Eq. tao0); the paper has no kappa formula of its own, so this is the standard kinetic form.
+ * rates: host, nT x N x nb (ps^-1); kappa: host, nT x 9 (row-major 3 x 3), W/(m K).  Uses the context's
+ * modes.  FP_ESTATE before the modes.
+ */
+int fp_kappa_rta(fp_ctx* ctx, int nT, const double* T, const double* rates, double* kappa);
+
+/*
  * Normal and Umklapp rates (the paper's separate normal and Umklapp RTA rate outputs, Appendix A): a process
  * q''' = q + s1 q' + s2 q'' + Q is normal when Q = 0 (Sec. 2.2).  Q depends on how each grid wavevector is
  * represented, which the paper does not state; here each is its shortest translate sum_a (g_a / N_a - m_a) b_a

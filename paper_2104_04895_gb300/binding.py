@@ -33,6 +33,11 @@ class fp_fc4(ctypes.Structure):
                 ("fc", ctypes.c_double * 81)]
 
 
+class fp_fc3(ctypes.Structure):
+    _fields_ = [("i", ctypes.c_int), ("j", ctypes.c_int), ("k", ctypes.c_int),
+                ("Rj", ctypes.c_int * 3), ("Rk", ctypes.c_int * 3), ("fc", ctypes.c_double * 27)]
+
+
 class fp_rates_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("window", ctypes.c_double), ("sigma_min", ctypes.c_double),
                 ("dq_mode", ctypes.c_int), ("mode_mask", ctypes.POINTER(ctypes.c_ubyte)),
@@ -51,7 +56,7 @@ class fp_stats(ctypes.Structure):
 
 
 EXPORTS = ["fp_version", "fp_default_opts", "fp_init", "fp_set_stream", "fp_modes", "fp_set_modes", "fp_rates4",
-           "fp_rates4_channels", "fp_rates4_nu", "fp_rates4_irreducible", "fp_star_table", "fp_rates4_device", "fp_rates4_noalloc", "fp_autotune", "fp_phase3", "fp_phase4", "fp_mlp_params_size",
+           "fp_rates4_channels", "fp_rates4_nu", "fp_set_fc3", "fp_rates3", "fp_kappa_rta", "fp_rates4_irreducible", "fp_star_table", "fp_rates4_device", "fp_rates4_noalloc", "fp_autotune", "fp_phase3", "fp_phase4", "fp_mlp_params_size",
            "fp_mlp_loss_grad", "fp_surrogate_default_opts", "fp_surrogate_fit", "fp_surrogate_rates", "fp_free",
            "fp_last_error"]
 
@@ -116,6 +121,12 @@ def load(path: str | None = None):
     L.fp_rates4_channels.argtypes = [vp, ctypes.c_int, dp, ctypes.c_double, ctypes.POINTER(fp_rates_opts), dp,
                                      ctypes.POINTER(fp_stats)]
     L.fp_rates4_channels.restype = ctypes.c_int
+    L.fp_set_fc3.argtypes = [vp, ctypes.c_int, ctypes.POINTER(fp_fc3)]
+    L.fp_set_fc3.restype = ctypes.c_int
+    L.fp_rates3.argtypes = L.fp_rates4_channels.argtypes
+    L.fp_rates3.restype = ctypes.c_int
+    L.fp_kappa_rta.argtypes = [vp, ctypes.c_int, dp, dp, dp]
+    L.fp_kappa_rta.restype = ctypes.c_int
     L.fp_rates4_nu.argtypes = L.fp_rates4_channels.argtypes
     L.fp_rates4_nu.restype = ctypes.c_int
     ip = ctypes.POINTER(ctypes.c_int)
@@ -208,7 +219,41 @@ class Context:
 
     @classmethod
     def from_crystal(cls, cr, device=0):
-        return cls(cr.lattice, cr.frac, cr.mass, cr.fc2_idx, cr.fc2_val, cr.fc4_idx, cr.fc4_val, cr.grid, device)
+        ctx = cls(cr.lattice, cr.frac, cr.mass, cr.fc2_idx, cr.fc2_val, cr.fc4_idx, cr.fc4_val, cr.grid, device)
+        if getattr(cr, "fc3_idx", None) is not None:
+            ctx.set_fc3(cr.fc3_idx, cr.fc3_val)
+        return ctx
+
+    def set_fc3(self, idx, val):
+        """fp_set_fc3: triplets idx (n3, 9) = i, j, k, Rj[3], Rk[3] and values (n3, 27) in eV/A^3."""
+        idx = np.asarray(idx)
+        val = np.asarray(val, np.float64)
+        arr = (fp_fc3 * max(1, len(idx)))()
+        for n, (ix, v) in enumerate(zip(idx, val)):
+            arr[n].i, arr[n].j, arr[n].k = int(ix[0]), int(ix[1]), int(ix[2])
+            for d in range(3):
+                arr[n].Rj[d], arr[n].Rk[d] = int(ix[3 + d]), int(ix[6 + d])
+            arr[n].fc[:] = [float(x) for x in v]
+        _check(self.L, self.h, self.L.fp_set_fc3(self.h, len(idx), arr))
+
+    def kappa_rta(self, temps, rates):
+        """fp_kappa_rta: kappa (nT, 3, 3) in W/(m K) from rates (nT, N, nb) in ps^-1."""
+        T = np.ascontiguousarray(temps, np.float64).reshape(-1)
+        r = np.ascontiguousarray(rates, np.float64).reshape(len(T), -1)
+        k = np.zeros((len(T), 3, 3))
+        _check(self.L, self.h, self.L.fp_kappa_rta(self.h, len(T), _dp(T), _dp(r), _dp(k)))
+        return k
+
+    def rates3(self, temps, scalebroad=1.0, **opts):
+        """fp_rates3: three-phonon rates (nT, N, nb) and stats."""
+        T = np.ascontiguousarray(temps, np.float64).reshape(-1)
+        o, keep = self.make_opts(**opts)
+        out = np.zeros((len(T), self.N, self.nb))
+        st = fp_stats()
+        rc = self.L.fp_rates3(self.h, len(T), _dp(T), float(scalebroad), ctypes.byref(o), _dp(out), ctypes.byref(st))
+        _check(self.L, self.h, rc)
+        del keep
+        return out, st.as_dict()
 
     def close(self):
         if getattr(self, "h", None):

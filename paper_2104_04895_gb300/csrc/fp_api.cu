@@ -143,6 +143,9 @@ void fp_free(fp_ctx* c) {
   dfree(c->d_rates);
   dfree(c->d_star);
   dfree(c->d_bzm);
+  dfree(c->d_t3_start);
+  dfree(c->d_t3_cell);
+  dfree(c->d_t3_fc);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);

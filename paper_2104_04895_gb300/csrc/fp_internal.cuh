@@ -117,6 +117,12 @@ struct fp_ctx {
   int* d_kl_grp = nullptr;
   double2* d_tw = nullptr;
   int* d_bzm = nullptr;  // [N][3] Brillouin-zone shifts (bz_shifts)
+  // third-order force constants (fp_set_fc3), grouped by atom triple
+  bool have_fc3 = false;
+  int n3 = 0;
+  int* d_t3_start = nullptr;   // [natoms^3 + 1]
+  int* d_t3_cell = nullptr;    // [n3][6] Rj, Rk
+  double* d_t3_fc = nullptr;   // [n3][27] Phi3 / sqrt(Mi Mj Mk)
   // modes
   bool have_modes = false;
   double* d_omega = nullptr;
