@@ -229,3 +229,30 @@ def v3(cryst, evec, q, q1, process):
     if rc != 0:
         raise ValueError("oracle_v3 rejected its arguments")
     return out[..., 0] + 1j * out[..., 1], q2.value
+
+
+# CODATA 2018 constants in the units of the rates (the same data as fp_oracle.c's ORC_HBAR / ORC_KB)
+_HBAR_EV_PS = 6.582119569e-4
+_KB_EV_K = 8.617333262e-5
+_KB_J_K = 1.380649e-23
+
+
+def kappa_rta(lattice, omega, vel, temps, rates):
+    """RTA lattice thermal conductivity (nT, 3, 3) in W/(m K), the kinetic form that the rates feed:
+    kappa_ab = k_B / (N V) sum_modes c(x) v_a v_b / rate, c(x) = x^2 e^x / (e^x - 1)^2, x = hbar w / (k_B T).
+    omega (N, nb) rad/ps, vel (N, nb, 3) A/ps, rates (nT, N, nb) ps^-1; modes with w = 0 or rate <= 0 are left out.
+    Units: k_B [J/K] (A/ps)^2 ps / A^3 = k_B * 1e4 * 1e-12 / 1e-30 W/(m K)."""
+    w = np.asarray(omega, float).reshape(-1)
+    v = np.asarray(vel, float).reshape(-1, 3)
+    r = np.asarray(rates, float).reshape(len(temps), -1)
+    N = np.asarray(omega).shape[0]
+    V = abs(np.linalg.det(np.asarray(lattice, float)))
+    out = np.zeros((len(temps), 3, 3))
+    for t, T in enumerate(temps):
+        for m in range(len(w)):
+            if not (w[m] > 0.0 and r[t, m] > 0.0):
+                continue
+            x = _HBAR_EV_PS * w[m] / (_KB_EV_K * T)
+            c = x * x * np.exp(x) / np.expm1(x) ** 2
+            out[t] += c / r[t, m] * np.outer(v[m], v[m])
+    return out * _KB_J_K * 1e4 * 1e-12 / 1e-30 / (N * V)
