@@ -142,10 +142,10 @@ __device__ __forceinline__ double exp_neg(double u, const double* tab) {
 
 // Shared-memory carve shared by the kernel and the host-side size query.
 struct Carve {
-  size_t E0, E1, E2, E3, Psi, T, Tw2, TwQ, QW, ncx;                           // complex elements
-  size_t Om0, Om1, Om2, Om3, V1, V2, V3, Sig, W0, W1, W2, W3, Red, Wp, ndbl, ExpT;  // doubles
+  size_t E0, E1, E2, E3, Psi, T, Tw2, TwQ, ncx;                           // complex elements
+  size_t Om0, Om1, Om2, Om3, V1, V2, V3, Sig, W0, W1, W2, W3, Red, Wp, QD, ndbl, ExpT;  // doubles
   size_t Hq, Lq, H1, L1, H2, L2, H3, L3, VH1, VL1, VH2, VL2, VH3, VL3, Sigf, F0, F1, F2, F3, nflt;  // floats
-  size_t KL, QI, nint;                                                        // ints
+  size_t KL, QI, EQ, nint;                                                        // ints
   size_t Mask;                                                                // bytes
   size_t bytes(size_t cx_size) const {
     return ncx * cx_size + ndbl * sizeof(double) + nflt * sizeof(float) + nint * sizeof(int) + Mask + 16;
@@ -154,6 +154,9 @@ struct Carve {
 
 // terms queued per warp in the screening phase (a power of two)
 constexpr int kQCap = 128;
+// entries queued per warp (a power of two, at least 64: the queue holds fewer than 32 before a j3 step adds
+// at most 32)
+constexpr int kEQCap = 64;
 // accumulator slots per lane: the j0 values that the 32 rows of one warp can span
 __host__ __device__ constexpr int acc_slots(int nb) { return nb == 3 ? 3 : 2; }
 
@@ -172,7 +175,6 @@ __host__ __device__ inline Carve make_carve(int nb, int J, int G, int nquart, in
   c.Tw2 = o; o += G;
   c.TwQ = o; o += nquart;
   const size_t nwarps = ((size_t)threads + 31) / 32;
-  c.QW = o; o += f32 ? 0 : nwarps * kQCap;  // FP64: queued vertices
   c.ncx = o;
   size_t d = 0;
   c.Om0 = d; d += J;
@@ -189,6 +191,7 @@ __host__ __device__ inline Carve make_carve(int nb, int J, int G, int nquart, in
   c.W3 = d; d += (size_t)nT * nb;
   c.Red = d; d += (size_t)threads * acc_slots(nb) * nT;
   c.Wp = d; d += f32 ? 0 : (size_t)threads * 4;  // FP64, one temperature: per-row weight products
+  c.QD = d; d += f32 ? 0 : nwarps * kQCap;         // FP64: |W|^2 of queued terms
   c.ExpT = d; d += f32 ? 0 : kExpTab;
   c.ndbl = d;
   size_t f = 0;
@@ -215,6 +218,7 @@ __host__ __device__ inline Carve make_carve(int nb, int J, int G, int nquart, in
   size_t k = 0;
   c.KL = k; k += na * na + 1 + G;
   c.QI = k; k += f32 ? 0 : nwarps * kQCap;  // FP64: queued term indices
+  c.EQ = k; k += f32 ? 0 : nwarps * kEQCap;  // FP64: queued entries
   c.nint = k;
   c.Mask = (size_t)J;
   return c;
@@ -405,7 +409,6 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
   C* sT = cx + cv.T;
   C* sTw2 = cx + cv.Tw2;
   C* sTwQ = cx + cv.TwQ;
-  C* sQW = cx + cv.QW;  // [warp][kQCap]
   double* db = reinterpret_cast<double*>(cx + cv.ncx);
   double* sOm0 = db + cv.Om0;
   double* sOm1 = db + cv.Om1;
@@ -422,6 +425,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
   double* sRed = db + cv.Red;
   double* sExpT = db + cv.ExpT;
   double* sWp = db + cv.Wp;  // [thread][4] (FP64, one temperature)
+  double* sQD = db + cv.QD;  // [warp][kQCap]
   float* fb = reinterpret_cast<float*>(db + cv.ndbl);
   float* sHq = fb + cv.Hq;
   float* sLq = fb + cv.Lq;
@@ -447,6 +451,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
   int* sKLs = ib + cv.KL;            // [NA*NA + 1]
   int* sKLg = sKLs + NA * NA + 1;    // [G]
   int* sQI = ib + cv.QI;             // [warp][kQCap]
+  int* sEQ = ib + cv.EQ;             // [warp][kEQCap]
   unsigned char* sMask = reinterpret_cast<unsigned char*>(ib + cv.nint);
 
   // the row this thread owns in the contraction and screening phases
@@ -458,6 +463,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
   constexpr int S = acc_slots(NB);
   const int lane = tid & 31;
   const int qbase = (tid >> 5) * kQCap;
+  const int ebase = (tid >> 5) * kEQCap;
   const int jj_lo = (tid & ~31) / NB2;  // the j0 of this warp's first row; its rows span jj_lo .. jj_lo + S - 1
 
   if constexpr (kF64)
@@ -510,9 +516,9 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
         acch[sl][t] = 0.f;
         accl[sl][t] = 0.f;
       }
-    // FP64 path: one queued term (vertex Wv; info = c | j3 << 3 | y << 7 | x << 11 | jj << 15): Gaussian,
-    // Bose weights and |W|^2 into the accumulator slot of its j0
-    auto consume = [&](const C Wv, const int info) {
+    // FP64 path: one queued term (|W|^2 and info = c | j3 << 3 | y << 7 | x << 11 | jj << 15): Gaussian and
+    // Bose weights into the accumulator slot of its j0
+    auto consume = [&](const double W2, const int info) {
       const int c = info & 7, j3 = (info >> 3) & 15, iy = (info >> 7) & 15, ix = (info >> 11) & 15;
       const int jq = info >> 15;
       const int slot = jq - jj_lo;
@@ -524,7 +530,6 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
       const int s1 = (p == 2) ? 1 : 0, s2 = (p == 0) ? 0 : 1;
       const int i1 = ordA ? ix : iy, i2 = ordA ? iy : ix;
       const int cls = (p == 0) ? 0 : (p == 2) ? 3 : ordA ? 1 : 2;
-      const double W2 = Wv.re * Wv.re + Wv.im * Wv.im;
       const double d64 = dw_fp64(c, sOm0[jq], sOm1[ix], sOm2[iy], sOm3[j3]);
       const double inv = sSig[2 * ent + 1];
       double delta = 1.0;
@@ -758,10 +763,6 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
           const float apy = ap + hy, apm = ap - hy, amm = am - hy;
           const float bpx = bp + hx, bpm = bp - hx, bmm = bm - hx;
           const float s0 = (h0 + hx) + hy;
-          C e2row[NB];
-#pragma unroll
-          for (int c = 0; c < NB; ++c) e2row[c] = sE2[y * NB + c];
-          const C* tb = sT + (size_t)(jq0 * NB + x) * (NB2 + 1);
           if constexpr (MAXT == 1) {
             // the four distinct products c_p (1/(n0 w0)) x leg weights of this row, per candidate class
             // (++ both orderings, +- ordering A, +- ordering B, -- both orderings), read by any lane
@@ -778,28 +779,27 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
           const float2* PA1 = sSigPM + 1 * NB2 + y * NB;
           const float2* PB0 = sSigPM + 2 * NB2 + x * NB;
           const float2* PB1 = sSigPM + 3 * NB2 + x * NB;
-          int qh = 0, qn = 0;  // warp-uniform queue head and length
-#pragma unroll 1
-          for (int j3 = 0; j3 < NB; ++j3) {
-            const float h3 = sH3[j3];
-            if (h3 == 0.f) continue;  // uniform: j3 and k2 are the same on all lanes
-            unsigned accm = 0;
-            C Wv = cmk<R>(unit ? 1 : 0, 0);
-            if (row_ok) {
-              const float sS = kRelS * (s0 + h3);
-              const float2 a0 = PA0[j3], a1 = PA1[j3], b0 = PB0[j3], b1 = PB1[j3];
-              unsigned band = 0;
-              FP_WINDOW_TEST()
-              if (accm && !unit) {
+          int qh = 0, qn = 0;  // warp-uniform term-queue head and length
+          int eh = 0, en = 0;  // warp-uniform entry-queue head and length
+          // lanes take up to 32 queued entries: W of each, then its accepted candidates into the term queue,
+          // which the warp evaluates 32 at a time
+          auto run_entries = [&](int count) {
+            unsigned ent = 0;
+            if (lane < count) ent = (unsigned)sEQ[ebase + ((eh + lane) & (kEQCap - 1))];
+            eh = (eh + count) & (kEQCap - 1);
+            en -= count;
+            double W2 = 1.0;
+            if (ent && !unit) {
+              const int ej3 = (ent >> 6) & 15, ey = (ent >> 10) & 15, ex = (ent >> 14) & 15, ejq = ent >> 18;
+              const C* tbe = sT + (size_t)(ejq * NB + ex) * (NB2 + 1) + ej3;
+              const C* e2 = sE2 + ey * NB;
+              C Wv = cmk<R>(0, 0);
 #pragma unroll
-                for (int c = 0; c < NB; ++c) cfma(Wv, e2row[c], tb[c * NB + j3]);
-              }
-              cnt0 += __popc(accm & 0x09u);
-              cnt1 += __popc(accm & 0x12u);
-              cnt2 += __popc(accm & 0x24u);
+              for (int c = 0; c < NB; ++c) cfma(Wv, e2[c], tbe[c * NB]);
+              W2 = Wv.re * Wv.re + Wv.im * Wv.im;
             }
-            // enqueue: lane offsets by an inclusive scan of the per-lane counts
-            const int nmy = __popc(accm);
+            unsigned m = ent & 63u;
+            const int nmy = __popc(m);
             int incl = nmy;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -808,16 +808,17 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
             }
             const int total = __shfl_sync(0xffffffffu, incl, 31);
             int pos = qn + incl - nmy;
-            const int info0 = (j3 << 3) | (y << 7) | (x << 11) | (jq0 << 15);
-            while (accm) {
-              const int c = __ffs(accm) - 1;
-              accm &= accm - 1;
+            const int info0 = (int)(((ent >> 6) & 15) << 3 | ((ent >> 10) & 15) << 7 | ((ent >> 14) & 15) << 11 |
+                                    (ent >> 18) << 15);
+            while (m) {
+              const int c = __ffs(m) - 1;
+              m &= m - 1;
               if (pos < kQCap) {
                 const int sl = (qh + pos) & (kQCap - 1);
-                sQW[qbase + sl] = Wv;
+                sQD[qbase + sl] = W2;
                 sQI[qbase + sl] = info0 | c;
               } else {
-                consume(Wv, info0 | c);  // queue full (rare): the producing lane evaluates the term
+                consume(W2, info0 | c);  // term queue full (rare): the producing lane evaluates the term
               }
               ++pos;
             }
@@ -825,15 +826,40 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
             __syncwarp();
             while (qn >= 32) {
               const int sl = (qh + lane) & (kQCap - 1);
-              consume(sQW[qbase + sl], sQI[qbase + sl]);
+              consume(sQD[qbase + sl], sQI[qbase + sl]);
               qh = (qh + 32) & (kQCap - 1);
               qn -= 32;
             }
             __syncwarp();
+          };
+#pragma unroll 1
+          for (int j3 = 0; j3 < NB; ++j3) {
+            const float h3 = sH3[j3];
+            if (h3 == 0.f) continue;  // uniform: j3 and k2 are the same on all lanes
+            unsigned accm = 0;
+            if (row_ok) {
+              const float sS = kRelS * (s0 + h3);
+              const float2 a0 = PA0[j3], a1 = PA1[j3], b0 = PB0[j3], b1 = PB1[j3];
+              unsigned band = 0;
+              FP_WINDOW_TEST()
+              cnt0 += __popc(accm & 0x09u);
+              cnt1 += __popc(accm & 0x12u);
+              cnt2 += __popc(accm & 0x24u);
+            }
+            // entries with an accepted candidate, one per lane at most, in lane order
+            const unsigned bal = __ballot_sync(0xffffffffu, accm != 0);
+            if (accm) {
+              const int pos = en + __popc(bal & ((1u << lane) - 1u));
+              sEQ[ebase + ((eh + pos) & (kEQCap - 1))] = (int)(accm | (j3 << 6) | (y << 10) | (x << 14) | (jq0 << 18));
+            }
+            en += __popc(bal);
+            __syncwarp();
+            while (en >= 32) run_entries(32);
           }
+          if (en > 0) run_entries(en);
           if (lane < qn) {
             const int sl = (qh + lane) & (kQCap - 1);
-            consume(sQW[qbase + sl], sQI[qbase + sl]);
+            consume(sQD[qbase + sl], sQI[qbase + sl]);
           }
           __syncwarp();
         } else {
