@@ -121,17 +121,17 @@ constexpr float kRelP = 1.0f / 4194304.0f;        // 2^-22: prefilter margin per
 constexpr float kAbsV = 1.0f / 1099511627776.0f;  // 2^-40: two-float velocity difference error per |v|_1
 
 // exp(-u) for the FP64 Gaussian, table-driven (P. T. P. Tang, ACM TOMS 15 (1989) 144-157): u = k h + r with
-// h = 1/32 and |r| <= h/2, exp(-u) = exp(-k h) exp(-r); exp(-k h) comes from a table of kExpTab entries
-// (0 <= u <= 4), exp(-r) from its Taylor polynomial of degree 6, whose truncation error (h/2)^7/7! < 5e-17 is
-// below half an ulp. Larger u (only when the window exceeds 2) takes exp().
-constexpr int kExpTab = 136;
-constexpr double kExpH = 1.0 / 32.0;
+// h = 1/64 and |r| <= h/2, exp(-u) = exp(-k h) exp(-r); exp(-k h) comes from a table of kExpTab entries
+// (0 <= u <= 4), exp(-r) from its Taylor polynomial of degree 5, whose truncation error (h/2)^6/6! < 4e-16 is
+// below two ulp. Larger u (only when the window exceeds 2) takes exp().
+constexpr double kSqrtPi = 1.7724538509055160273;  // sqrt(pi)
+constexpr int kExpTab = 264;
+constexpr double kExpH = 1.0 / 64.0;
 __device__ __forceinline__ double exp_neg(double u, const double* tab) {
   if (!(u <= 4.0)) return exp(-u);
-  const int k = __double2int_rn(u * 32.0);
+  const int k = __double2int_rn(u * 64.0);
   const double s = fma((double)k, kExpH, -u);  // -r, exact
-  double p = 1.0 / 720.0;
-  p = fma(p, s, 1.0 / 120.0);
+  double p = 1.0 / 120.0;
   p = fma(p, s, 1.0 / 24.0);
   p = fma(p, s, 1.0 / 6.0);
   p = fma(p, s, 0.5);
@@ -532,10 +532,11 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
       const int cls = (p == 0) ? 0 : (p == 2) ? 3 : ordA ? 1 : 2;
       const double d64 = dw_fp64(c, sOm0[jq], sOm1[ix], sOm2[iy], sOm3[j3]);
       const double inv = sSig[2 * ent + 1];
-      double delta = 1.0;
+      // sqrt(pi) delta; the 1/sqrt(pi) is folded into the row weights (one temperature) or the multiplicity
+      double delta = kSqrtPi;
       if (inv >= 0.0) {
         const double xx = d64 * inv;
-        delta = exp_neg(xx * xx, sExpT) * inv * kInvSqrtPi;
+        delta = exp_neg(xx * xx, sExpT) * inv;
       }
       if constexpr (MAXT == 1) {
         const double term = (W2 * delta) * sWp[4 * (jq * NB2 + ix * NB + iy) + cls] * sW3[j3];
@@ -543,7 +544,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
         for (int sl = 0; sl < S; ++sl)
           if (sl == slot) acc[sl][0] += term;
       } else {
-        const double base = (p == 2 ? (1.0 / 6.0) : 0.5) * W2 * delta;
+        const double base = (p == 2 ? kInvSqrtPi / 6.0 : 0.5 * kInvSqrtPi) * W2 * delta;
         const double* wq1 = ordA ? sW1 : sW2;
         const double* wq2 = ordA ? sW2 : sW1;
 #pragma unroll
@@ -769,10 +770,11 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
             if (row_ok) {
               const double f0 = sW0[jq0], a1 = sW1[2 * x], b1 = sW1[2 * x + 1], a2 = sW2[2 * y], b2 = sW2[2 * y + 1];
               double* wp = sWp + 4 * tid;
-              wp[0] = 0.5 * f0 * (a1 * a2);
-              wp[1] = 0.5 * f0 * (a1 * b2);
-              wp[2] = 0.5 * f0 * (a2 * b1);
-              wp[3] = (1.0 / 6.0) * f0 * (b1 * b2);
+              // with the 1/sqrt(pi) of the Gaussian
+              wp[0] = 0.5 * kInvSqrtPi * f0 * (a1 * a2);
+              wp[1] = 0.5 * kInvSqrtPi * f0 * (a1 * b2);
+              wp[2] = 0.5 * kInvSqrtPi * f0 * (a2 * b1);
+              wp[3] = (kInvSqrtPi / 6.0) * f0 * (b1 * b2);
             }
           }
           const float2* PA0 = sSigPM + 0 * NB2 + y * NB;
