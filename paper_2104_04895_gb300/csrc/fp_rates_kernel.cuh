@@ -16,9 +16,10 @@
 //   W[j0][j1][j2][j3]       = sum_{(k g)} e_{kg}(k2,j2) T[..][(k g)][j3]
 // Groups collect quartets with equal (atom k, atom l, D = R_k - R_l).  Thread r < J*nb^2 owns the row
 // (j0, j1, c) when it builds A and T (registers -> shared T) and the row (j0, j1 = x, j2 = y) when it
-// screens the nb entries (x, y, j3) of that row and builds W (registers) where a candidate is accepted.
-// The FP64 path then hands each accepted term to a per-warp queue that the warp evaluates 32 at a time;
-// the FP32 path evaluates a lane's accepted terms in that lane.
+// screens the nb entries (x, y, j3) of that row.  The FP64 path queues the entries with an accepted
+// candidate per warp; the warp forms their W 32 at a time and queues their accepted terms, which it
+// evaluates 32 at a time.  The FP32 path builds W in the lane's registers and evaluates the lane's
+// accepted terms in that lane.
 //
 // Window and Gaussian (Sec. 2.4): the decision |dw| <= window * max(sigma, sigma_min) is the FP64 one,
 // with dw = ((w0 +- w') +- w'') - w''' and sigma = (sb * sqrt((dx^2 + dy^2) + dz^2)) * dq evaluated in that
@@ -748,9 +749,10 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
         }
         __syncthreads();
         if constexpr (kF64) {
-          // ---- phase 3 (FP64 path): every lane screens the window of its row (jj, x, y) for all j3; the accepted
-          // (entry, candidate) terms enter a per-warp queue and the warp evaluates them 32 at a time, so the
-          // Gaussian and Bose arithmetic runs on full warps however unevenly the accepted terms fall on lanes
+          // ---- phase 3 (FP64 path): every lane screens the window of its row (jj, x, y) for all j3; entries with
+          // an accepted candidate enter a per-warp entry queue, whose entries the warp takes 32 at a time to form
+          // W and to append their accepted terms to a per-warp term queue, evaluated 32 at a time: W, the
+          // Gaussian and the Bose arithmetic run on full warps however unevenly the accepted terms fall on lanes
           const int x = rj1, y = rc;
           const int jq0 = active ? rjj : 0;
           const bool row_ok = active && sH1[x] != 0.f && sH2[y] != 0.f;
