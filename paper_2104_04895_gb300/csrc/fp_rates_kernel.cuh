@@ -867,7 +867,8 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
           }
           __syncwarp();
         } else {
-          // ---- phase 3 (FP32 path): W row (jj, x, y) in registers, then window, Gaussian and Bose weights
+          // ---- phase 3 (FP32 path): window of the row (jj, x, y), W in registers where a candidate is accepted,
+          // then Gaussian and Bose weights
           if (active) {
             const int x = rj1, y = rc;
             const double w0 = sOm0[rjj];
@@ -877,9 +878,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
             const unsigned cand = ((k1 != k2 && !unit) ? 0x3Fu : 0x07u) & a.cand_mask &
                                   (a.nu_select == 0 ? 0x3Fu : a.nu_select == 1 ? ~s_umask : s_umask);
             if (hx != 0.f && hy != 0.f) {
-              C e2row[NB];
-#pragma unroll
-              for (int c = 0; c < NB; ++c) e2row[c] = sE2[y * NB + c];
+              const C* e2row = sE2 + y * NB;  // read from shared memory where W is formed
               const C* tb = sT + (size_t)(rjj * NB + x) * (NB2 + 1);
               const float ap = h0 + hx, am = h0 - hx, bp = h0 + hy, bm = h0 - hy;
               const float apy = ap + hy, apm = ap - hy, amm = am - hy;
