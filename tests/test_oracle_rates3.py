@@ -77,3 +77,46 @@ def test_quadratic_in_phi3():
     c0.fc3_val = 0.0 * cr.fc3_val
     r0, _ = oracle.rates3(c0, w, e, v, sel=sel)
     assert np.all(r0 == 0.0) and np.all(r > 0.0)
+
+
+HBAR_SI = 1.054571817e-34     # J s
+KB_SI = 1.380649e-23          # J/K
+EV = 1.602176634e-19
+AMU_SI = 1.66053906660e-27
+ANG = 1e-10
+
+
+def test_single_q_closed_form_in_si_units(rng):
+    """One q-point (1x1x1 grid), injected integer frequencies, v = 0: only exactly energy-conserving terms
+    enter, each with delta := 1 ps. The rate then follows from Eqs. tao0 and 3phgamma written out in SI
+    units with the brute-force supercell vertex, which pins the prefactor hbar pi / 4, the multiplicities
+    1 and 1/2, the two Bose forms and the unit conversion term by term."""
+    cr = synth.diamond_si((1, 1, 1))
+    nb = cr.nb
+    omega = np.array([[1.0, 2.0, 3.0, 3.0, 5.0, 8.0]])
+    A = rng.normal(size=(nb, nb)) + 1j * rng.normal(size=(nb, nb))
+    Q, _ = np.linalg.qr(A)
+    evec = Q.T[None, :, :].copy()
+    vel = np.zeros((1, nb, 3))
+    T = 300.0
+    rates, acc = oracle.rates3(cr, omega, evec, vel, temps=[T], scalebroad=1.0)
+    P3 = brute.supercell_phi3(cr)
+    vconv = EV / ANG**3 / AMU_SI**1.5          # eV/(A^3 amu^1.5) -> J/(m^3 kg^1.5)
+    n = 1.0 / np.expm1(HBAR_SI * omega[0] * 1e12 / (KB_SI * T))
+    count = np.zeros(2)
+    for lam in range(nb):
+        expect = 0.0
+        for pr, s1 in ((0, 1), (1, -1)):
+            V = brute.vertex3(cr, P3, evec, 0, 0, 0, conj1=s1 < 0)
+            for j1 in range(nb):
+                for j2 in range(nb):
+                    if omega[0, lam] + s1 * omega[0, j1] - omega[0, j2] != 0.0:
+                        continue
+                    count[pr] += 1
+                    B = (n[j1] - n[j2]) if pr == 0 else (n[j1] + n[j2] + 1.0)
+                    wsi = omega[0, [lam, j1, j2]] * 1e12
+                    # Gamma = hbar pi / 4 B |V|^2 delta / (w w' w''); delta = 1 ps; 1/N = 1; the - sum has 1/2
+                    gam = HBAR_SI * np.pi / 4.0 * B * abs(V[lam, j1, j2] * vconv) ** 2 * 1e-12 / np.prod(wsi)
+                    expect += (1.0 if pr == 0 else 0.5) * gam
+        assert rates[0, lam] == pytest.approx(expect * 1e-12, rel=1e-9, abs=1e-300), lam
+    assert np.array_equal(acc, count) and acc.min() > 0
