@@ -1,5 +1,5 @@
-// Stars of the q-grid under a point group and time reversal (host only): the map from every grid point
-// to the representative of its star, used by fp_rates4_irreducible.
+// Host-only grid geometry: the stars of the q-grid under a point group and time reversal (fp_star_table, used by
+// fp_rates4_irreducible) and the Brillouin-zone representatives behind the normal/Umklapp split (bz_shifts).
 #include <cstdlib>
 #include <vector>
 
