@@ -246,3 +246,22 @@ def test_normal_and_umklapp_split_the_rate():
     u1, c1 = oracle.rates4(one, w1, e1, v1, nu="umklapp")
     assert np.array_equal(n1, f1) and np.array_equal(b1, a1)
     assert np.all(u1 == 0.0) and np.all(c1 == 0.0)
+
+
+def test_umklapp_classification_is_point_group_invariant(rng):
+    """On an odd simple-cubic grid no wavevector lies on the zone boundary, so the shortest translates are unique
+    and the normal/Umklapp split must be invariant under the 48 cubic operations applied to all partners."""
+    cr = synth.simple_cubic((3, 3, 3), symmetric=True)
+    ops = synth.point_group_ops(cr)
+    n = 3
+    idx = lambda g: int(((g[0] % n) * n + g[1] % n) * n + g[2] % n)
+    G = np.array(np.unravel_index(np.arange(cr.nq), cr.grid)).T
+    seen = set()
+    for _ in range(30):
+        q, q1, q2 = (int(x) for x in rng.integers(0, cr.nq, size=3))
+        for pr in range(3):
+            u = oracle.umklapp(cr, q, q1, q2, pr)
+            seen.add(u)
+            for R in ops[::5]:
+                assert oracle.umklapp(cr, idx(R @ G[q]), idx(R @ G[q1]), idx(R @ G[q2]), pr) == u
+    assert seen == {0, 1}
