@@ -39,9 +39,11 @@ def build(force: bool = False) -> str:
 
 
 def lib():
+    """The oracle library.  FP_ORACLE_LIB, when set, names another build of fp_oracle.c to load instead (the
+    mutation tests use it to check that the pins fail on a deliberately broken copy of the oracle)."""
     global _LIB
     if _LIB is None:
-        L = ctypes.CDLL(build())
+        L = ctypes.CDLL(os.environ.get("FP_ORACLE_LIB") or build())
         dp = ctypes.POINTER(ctypes.c_double)
         ip = ctypes.POINTER(ctypes.c_int)
         L.oracle_rates4.restype = ctypes.c_int
