@@ -254,7 +254,7 @@ def main():
     value = cands_step * args.steps / (total_ms * 1e-3)
     # algorithmic flops per launch: the vertex work of this factorization (fp_stats.flops) plus the
     # accumulation of every accepted term at every temperature (Gaussian, Bose weights, |W|^2: 25 flops)
-    acc_flops = FLOPS_PER_ACCEPTED_TERM * sum(st["accepted"]) * nT
+    acc_flops = FLOPS_PER_ACCEPTED_TERM * st["terms_executed"] * nT
     achieved_tflops = (st["flops"] + acc_flops) / (kms * 1e-3) / 1e12
     peak = FP64_PEAK_TFLOPS if main_prec == binding.FP_PREC_FP64 else FP32_PEAK_TFLOPS
     other = None
@@ -263,7 +263,7 @@ def main():
                                            args.steps, args.warmup, barrier)
         o_ms = max_over_ranks(o_ms, dist if ws > 1 else None, dev)
         o_peak = FP64_PEAK_TFLOPS if other_prec == binding.FP_PREC_FP64 else FP32_PEAK_TFLOPS
-        o_ach = (o_st["flops"] + FLOPS_PER_ACCEPTED_TERM * sum(o_st["accepted"]) * nT) / (o_kms * 1e-3) / 1e12
+        o_ach = (o_st["flops"] + FLOPS_PER_ACCEPTED_TERM * o_st["terms_executed"] * nT) / (o_kms * 1e-3) / 1e12
         other = {"precision": "fp64" if other_prec == binding.FP_PREC_FP64 else "mixed",
                  "value": cands_step * args.steps / (o_ms * 1e-3), "unit": "process-terms/s",
                  "s_per_rate_set": o_ms / args.steps * 1e-3, "tile": o_st["tile"],
@@ -322,6 +322,8 @@ def main():
                        f"{cr.name} {args.grid[0]}x{args.grid[1]}x{args.grid[2]} (profiling case)",
                        "precision": args.precision,
                        "candidates_per_step": cands_step, "accepted_per_step": st["accepted"],
+                       "candidates_executed_per_step": st["candidates_executed"],
+                       "time_reversal": "one q of each pair {q, -q} evaluated, rates written at both",
                        "l2": "flushed between timed steps (256 MB write)", "tile": st["tile"],
                        "autotuned_mixed_tile": tuned,
                        "parallelism": f"q-partition over {ws} GPU(s)"},

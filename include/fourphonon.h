@@ -75,15 +75,30 @@ typedef struct {
                                       (redistribution), bit 2 -- (splitting); 0 = all three */
   int nu_select;                   /* 0: all processes; 1: normal only; 2: Umklapp only (Sec. 2.2: Q = 0 or not;
                                       the representatives are described at fp_rates4_nu) */
+  int no_time_reversal;            /* 0 (default): time reversal (e^{-lambda} = conj e^{lambda}, Sec. 2.2) makes
+                                      the rate of (-q, j) equal to that of (q, j) term by term (the terms at -q are
+                                      those at q with every wavevector negated: equal frequencies, |V4|^2 and
+                                      broadening), so one point of each pair {q, -q} is evaluated and its rates are
+                                      written at both (up to the order of the sum, the rates at -q are those an
+                                      evaluation at -q gives; accepted counts are exact); 1: evaluate every
+                                      selected q.  The normal/Umklapp split (nu_select != 0) evaluates every q,
+                                      because a zone-boundary tie breaks the symmetry of the representatives. */
 } fp_rates_opts;
 
 /* Counters of one fp_rates4 call. */
 typedef struct {
-  double candidates;   /* process terms examined: 3 * (selected modes) * N^2 * nb^3 */
-  double accepted[3];  /* terms inside the energy window for ++, +-, -- */
-  double flops;        /* vertex assembly + contraction flops issued (8 per complex multiply-add) */
+  double candidates;   /* process terms of the selected modes: (processes) * (selected modes) * N^2 * nb^3 */
+  double accepted[3];  /* terms of the selected modes inside the energy window for ++, +-, -- */
+  double flops;        /* vertex assembly + contraction flops executed (8 per complex multiply-add): the
+                          hoisted prologue and assembly per evaluated item and q'-pair, and one nb-term
+                          contraction per vertex entry formed (vertex_entries) */
   double ms;           /* device time of the rate kernels (CUDA events on the context stream) */
   int tile[4];         /* block_j0, k1_tile, threads, CTAs launched */
+  double candidates_executed;  /* candidates the kernel screened: those of the evaluated rows (time reversal
+                                  evaluates one point of each pair {q, -q}) */
+  double vertex_entries;       /* vertex entries W(j0, j1, j2, j3) formed: those with an accepted candidate */
+  double terms_executed;       /* accepted terms the kernel evaluated (Gaussian, Bose factors, |W|^2), all
+                                  processes; accepted[] counts each once per selected mode it stands for */
 } fp_stats;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -156,7 +171,10 @@ int fp_autotune(fp_ctx* ctx, int nT, const double* T, double scalebroad, fp_rate
  * every GPU loading the library holds until the process exits.  The q'-tile is enlarged automatically
  * to fit; a problem that still needs more than 16 MiB returns FP_EINVAL with the required size in
  * fp_last_error() (use fp_rates4_device for it).  The first call on a device looks up the array's
- * device address on that device; make that first call before starting any stream capture.  Every call
+ * device address on that device; make that first call before starting any stream capture.  With CUDA's
+ * lazy module loading (the default) that first call may also load the library's device code on the device
+ * and reserve the array there, which is device memory taken then; make a warm-up call before the phase in
+ * which nothing may be allocated.  Every call
  * shares the array (counters are cleared on each call), so calls whose GPU work overlaps -- other
  * streams, other contexts on the same device, other host threads -- race and must be serialised.
  */

@@ -43,16 +43,18 @@ class fp_rates_opts(ctypes.Structure):
                 ("dq_mode", ctypes.c_int), ("mode_mask", ctypes.POINTER(ctypes.c_ubyte)),
                 ("q_begin", ctypes.c_int), ("q_end", ctypes.c_int), ("block_j0", ctypes.c_int),
                 ("k1_tile", ctypes.c_int), ("threads", ctypes.c_int), ("no_graph", ctypes.c_int),
-                ("process_mask", ctypes.c_int), ("nu_select", ctypes.c_int)]
+                ("process_mask", ctypes.c_int), ("nu_select", ctypes.c_int), ("no_time_reversal", ctypes.c_int)]
 
 
 class fp_stats(ctypes.Structure):
     _fields_ = [("candidates", ctypes.c_double), ("accepted", ctypes.c_double * 3), ("flops", ctypes.c_double),
-                ("ms", ctypes.c_double), ("tile", ctypes.c_int * 4)]
+                ("ms", ctypes.c_double), ("tile", ctypes.c_int * 4), ("candidates_executed", ctypes.c_double),
+                ("vertex_entries", ctypes.c_double), ("terms_executed", ctypes.c_double)]
 
     def as_dict(self):
         return {"candidates": self.candidates, "accepted": list(self.accepted), "flops": self.flops,
-                "ms": self.ms, "tile": list(self.tile)}
+                "ms": self.ms, "tile": list(self.tile), "candidates_executed": self.candidates_executed,
+                "vertex_entries": self.vertex_entries, "terms_executed": self.terms_executed}
 
 
 EXPORTS = ["fp_version", "fp_default_opts", "fp_init", "fp_set_stream", "fp_modes", "fp_set_modes", "fp_rates4",
@@ -297,7 +299,8 @@ class Context:
 
     @staticmethod
     def make_opts(precision=FP_PREC_FP64, window=2.0, sigma_min=1e-10, dq_mode=0, mode_mask=None, q_begin=0,
-                  q_end=0, block_j0=0, k1_tile=0, threads=0, no_graph=0, process_mask=0, nu_select=0):
+                  q_end=0, block_j0=0, k1_tile=0, threads=0, no_graph=0, process_mask=0, nu_select=0,
+                  no_time_reversal=0):
         o = fp_rates_opts()
         o.precision, o.window, o.sigma_min, o.dq_mode = int(precision), float(window), float(sigma_min), int(dq_mode)
         o.q_begin, o.q_end, o.block_j0, o.k1_tile, o.threads = int(q_begin), int(q_end), int(block_j0), \
@@ -305,6 +308,7 @@ class Context:
         o.no_graph = int(no_graph)
         o.process_mask = int(process_mask)
         o.nu_select = int(nu_select)
+        o.no_time_reversal = int(no_time_reversal)
         keep = None
         if mode_mask is not None:
             keep = np.ascontiguousarray(mode_mask, np.uint8)

@@ -416,6 +416,8 @@ static int validate_opts(fp_ctx* c, int nT, const double* T, double sb, const fp
   if (o->process_mask < 0 || o->process_mask > 7)
     return fail(c, FP_EINVAL, "fp_rates4: process_mask must be in [0, 7]");
   if (o->nu_select < 0 || o->nu_select > 2) return fail(c, FP_EINVAL, "fp_rates4: nu_select must be 0, 1 or 2");
+  if (o->no_time_reversal != 0 && o->no_time_reversal != 1)
+    return fail(c, FP_EINVAL, "fp_rates4: no_time_reversal must be 0 or 1");
   return FP_OK;
 }
 
@@ -425,12 +427,15 @@ static int rates_impl(fp_ctx* c, int nT, const double* T, double sb, const fp_ra
   int rc = validate_opts(c, nT, T, sb, user, &o);
   if (rc) return rc;
   FP_CUDA(c, cudaSetDevice(c->device));
-  fp::Plan p;
   std::string err;
-  rc = fp::plan_rates(c, o, nT, 0, &p, &err);
+  fp::Selection sel;
+  rc = fp::make_selection(c, o, true, &sel, &err);
   if (rc) return fail(c, rc, "fp_rates4: " + err);
-  size_t sz[13], total = 0;
-  fp::scratch_sizes(c, p, nT, o.mode_mask != nullptr, sz);
+  fp::Plan p;
+  rc = fp::plan_rates(c, o, nT, sel, 0, &p, &err);
+  if (rc) return fail(c, rc, "fp_rates4: " + err);
+  size_t sz[fp::kScratchParts], total = 0;
+  fp::scratch_sizes(c, p, nT, sz);
   for (size_t x : sz) total += x;
   if (c->scratch_cap < total) {
     dfree(c->d_scratch);
@@ -438,31 +443,11 @@ static int rates_impl(fp_ctx* c, int nT, const double* T, double sb, const fp_ra
     FP_CUDA(c, dalloc(&c->d_scratch, total));
     c->scratch_cap = total;
   }
-  unsigned char* b = c->d_scratch;
-  size_t off[13];
-  size_t acc = 0;
-  for (int i = 0; i < 13; ++i) {
-    off[i] = acc;
-    acc += sz[i];
-  }
-  fp::Scratch sc;
-  sc.counters = reinterpret_cast<unsigned long long*>(b + off[0]);
-  sc.T = reinterpret_cast<double*>(b + off[1]);
-  sc.mask = o.mode_mask ? b + off[2] : nullptr;
-  sc.wt = reinterpret_cast<double*>(b + off[3]);
-  sc.partial = reinterpret_cast<double*>(b + off[4]);
-  sc.omh = reinterpret_cast<float*>(b + off[5]);
-  sc.oml = reinterpret_cast<float*>(b + off[6]);
-  sc.velh = reinterpret_cast<float*>(b + off[7]);
-  sc.vell = reinterpret_cast<float*>(b + off[8]);
-  sc.evf = reinterpret_cast<float2*>(b + off[9]);
-  sc.qfcf = reinterpret_cast<float*>(b + off[10]);
-  sc.twf = reinterpret_cast<float2*>(b + off[11]);
-  sc.wtf = reinterpret_cast<float*>(b + off[12]);
-  unsigned long long counts[4] = {0, 0, 0, 0};
-  rc = fp::run_rates(c, o, p, sc, nT, T, sb, d_out, counts, o.no_graph == 0, &err);
+  const fp::Scratch sc = fp::carve_scratch(c->d_scratch, sz);
+  unsigned long long counts[fp::kCounters] = {0};
+  rc = fp::run_rates(c, o, sel, p, sc, nT, T, sb, d_out, counts, o.no_graph == 0, &err);
   if (rc) return fail(c, rc, "fp_rates4: " + err);
-  if (stats) fp::fill_stats(c, o, p, counts, stats);
+  if (stats) fp::fill_stats(c, o, sel, p, counts, stats);
   return FP_OK;
 }
 
@@ -614,6 +599,9 @@ int rates_passes(fp_ctx* c, int nT, const double* T, double sb, const fp_rates_o
     sum.candidates += st.candidates;
     for (int k = 0; k < 3; ++k) sum.accepted[k] += st.accepted[k];
     sum.flops += st.flops;
+    sum.candidates_executed += st.candidates_executed;
+    sum.vertex_entries += st.vertex_entries;
+    sum.terms_executed += st.terms_executed;
     sum.ms += st.ms;
     std::memcpy(sum.tile, st.tile, sizeof(sum.tile));
   }

@@ -29,8 +29,16 @@ constexpr int kMaxT = 8;    // temperatures per call
 struct RatesArgs {
   int N, nb, natoms, nT, L, G, nquart;
   int grid[3], Lfac[3];
-  int J, t1, nchunk, ntile, q_begin, nq_sel;
+  int J, t1, nchunk, ntile, nq_sel;
   long long n_items;
+  const int* qlist;          // [nq_sel] the q-points the kernel evaluates (work item -> q)
+  const unsigned char* mult; // [N*nb] selected modes each evaluated row stands for: 0, 1, or 2 when the row's
+                             // rate is also written at -q (time reversal); weights the accepted counts
+  // reduction: outputs q in [q_out_begin, q_out_begin + q_out_n); a selected mode (sel) of q takes the partial
+  // sums of the evaluated point qlist[qpos[q]] (q itself, or -q under time reversal)
+  int q_out_begin, q_out_n;
+  const int* qpos;           // [N]
+  const unsigned char* sel;  // [N*nb]
   const double* omega;       // [N][nb]
   const double2* evec;       // [N][nb][nb]
   const double* vel;         // [N][nb][3]
@@ -43,7 +51,6 @@ struct RatesArgs {
   const int* kl_start;       // [natoms^2 + 1]
   const int* kl_grp;         // [G]
   const double2* tw;         // [L]: exp(2 pi i m / L)
-  const unsigned char* mask; // [N*nb] or null
   // FP32 copies prepared once per call (prep_kernel)
   const float* omh;          // [N*nb] two-float frequencies: omh + oml = omega
   const float* oml;
@@ -58,7 +65,8 @@ struct RatesArgs {
   double rec[9];
   double* partial;           // [n_items][J][nT]
   unsigned long long* counter;
-  unsigned long long* counts; // [3]
+  unsigned long long* counts; // [5]: accepted ++, +-, -- (weighted by mult), vertex entries W formed, accepted
+                              // terms evaluated
   int unit_vertex;           // 1: |W|^2 = 1 (weighted phase space), q' on a stride, ordered (q', q'') pairs
   int k1_stride;             // q' stride of the unit-vertex mode
   unsigned cand_mask;        // candidates summed (bit c = ordering * 3 + process), from process_mask
@@ -66,18 +74,40 @@ struct RatesArgs {
   const int* bzm;            // [N][3] Brillouin-zone shifts of the grid points (normal/Umklapp reading)
 };
 
+// Which q-points a rates call evaluates, and for which modes.  Time reversal (e^{-lambda} = conj e^{lambda},
+// Sec. 2.2) makes the rate of (-q, j) equal to that of (q, j) term by term: the terms at -q are those at q with
+// every wavevector negated, with the same frequencies, |V|^2 and broadening.  With `fold` the kernel evaluates
+// one point of each pair {q, -q} (the smaller index) and the reduction writes both.
+struct Selection {
+  bool fold = false;
+  int q_out_begin = 0, q_out_end = 0;
+  std::vector<int> qlist;           // evaluated q-points, ascending
+  std::vector<int> qpos;            // [N] index in qlist of the point evaluated for q (-1: none)
+  std::vector<unsigned char> mult;  // [N*nb] selected modes an evaluated row stands for (0, 1, 2)
+  std::vector<unsigned char> sel;   // [N*nb] 1 = the rate of this mode is written
+  double n_sel = 0;                 // selected modes
+  double n_exec = 0;                // evaluated rows with mult > 0
+  long long active_chunks = 0;      // (evaluated q, branch chunk) pairs with a row of mult > 0 (set by plan_rates)
+};
+
 // Tile plan of one rates call.
 struct Plan {
-  int J, threads, t1, nchunk, ntile, nq_sel, q_begin, q_end, ctas;
+  int J, threads, t1, nchunk, ntile, nq_sel, ctas;
   long long n_items;
   size_t smem;
 };
 
-// Device working memory of one rates call (owned by the caller of run_rates).
+// Device working memory of one rates call (owned by the caller of run_rates), in the order of scratch_sizes.
+constexpr int kScratchParts = 16;
+constexpr int kScratchPartial = 7;  // index of the per-item partial sums
+constexpr int kCounters = 8;        // queue, accepted ++, +-, --, vertex entries, terms evaluated, spare
 struct Scratch {
-  unsigned long long* counters;  // [4]: queue, accepted ++, +-, --
+  unsigned long long* counters;  // [kCounters]
   double* T;                     // [kMaxT]
-  unsigned char* mask;           // [N*nb] or null
+  unsigned char* mult;           // [N*nb]
+  unsigned char* sel;            // [N*nb]
+  int* qlist;                    // [N]
+  int* qpos;                     // [N]
   double* wt;                    // [nT][N*nb][3]
   double* partial;               // [n_items][J][nT]
   float* omh;                    // [N*nb]
@@ -157,22 +187,28 @@ cudaError_t launch_modes(fp_ctx* c, cudaStream_t s);
 cudaError_t launch_weights(fp_ctx* c, int nT, const double* d_T, double* d_wt, cudaStream_t s);
 
 // Rate path (fp_rates.cu).
+// The evaluated q-points and mode weights of a call: the q range and mode mask of `o`, folded by time reversal
+// unless o.no_time_reversal or o.nu_select is set or fold_allowed is false.  FP_EINVAL on a bad q range.
+int make_selection(const fp_ctx* c, const fp_rates_opts& o, bool fold_allowed, Selection* s, std::string* err);
 // Validate options and choose tiles; `partial_budget` (bytes, 0 = unlimited) enlarges the q'-tile until the
 // per-item partial sums fit.  Returns FP_OK or an FP_E* code with a message in *err.
-int plan_rates(fp_ctx* c, const fp_rates_opts& o, int nT, size_t partial_budget, Plan* p, std::string* err);
-// Byte sizes of the Scratch buffers of a plan (in the order of the Scratch fields).
-void scratch_sizes(const fp_ctx* c, const Plan& p, int nT, bool with_mask, size_t sizes[13]);
-// Enqueue weights, FP32 prep, the persistent rate kernel and the reduction on c->stream, then wait and
-// return the accepted counts.  d_out: nT x N x nb doubles (zeroed here).
+int plan_rates(fp_ctx* c, const fp_rates_opts& o, int nT, Selection& sel, size_t partial_budget, Plan* p,
+               std::string* err);
+// Byte sizes of the Scratch buffers of a plan, in the order of the Scratch fields (each rounded up to 256).
+void scratch_sizes(const fp_ctx* c, const Plan& p, int nT, size_t sizes[kScratchParts]);
+// Scratch pointers laid out from `base` with the sizes of scratch_sizes.
+Scratch carve_scratch(unsigned char* base, const size_t sizes[kScratchParts]);
+// Upload the selection, enqueue weights, FP32 prep, the persistent rate kernel and the reduction on c->stream,
+// then wait and return the counters.  d_out: nT x N x nb doubles (zeroed here).
 // use_graph: capture the device part once per set of launch parameters and replay it as a CUDA graph.
-int run_rates(fp_ctx* c, const fp_rates_opts& o, const Plan& p, const Scratch& s, int nT, const double* T,
-              double sb, double* d_out, unsigned long long counts[4], bool use_graph, std::string* err,
-              int unit_stride = 0);
+int run_rates(fp_ctx* c, const fp_rates_opts& o, const Selection& sel, const Plan& p, const Scratch& s, int nT,
+              const double* T, double sb, double* d_out, unsigned long long counts[kCounters], bool use_graph,
+              std::string* err, int unit_stride = 0);
 // Sampled four-phonon weighted phase space of every mode (surrogate feature): the rate sum with |W|^2 = 1
 // over q' on a stride (ordered pairs), scaled to the full grid; d_out: nT x N x nb, mixed precision.
 int phase4_sampled(fp_ctx* c, int nT, const double* T, double sb, int stride, double* d_out, std::string* err);
 // Brillouin-zone shifts of the grid points (fp_sym.cu), N x 3
 void bz_shifts(const int grid[3], const double rec[9], int* out);
-void fill_stats(const fp_ctx* c, const fp_rates_opts& o, const Plan& p, const unsigned long long counts[4],
-                fp_stats* st);
+void fill_stats(const fp_ctx* c, const fp_rates_opts& o, const Selection& sel, const Plan& p,
+                const unsigned long long counts[kCounters], fp_stats* st);
 }  // namespace fp

@@ -12,7 +12,9 @@
 // kScratchBytes of it until the process exits.  Host code must not use its name as a device address
 // (in host code it is only a stand-in symbol); the device address is obtained once per device with
 // cudaGetSymbolAddress, during the first call on that device, with that device current.  That first
-// call should therefore happen before any stream capture is started.  All calls share the array and
+// call should therefore happen before any stream capture is started.  Under lazy module loading (CUDA's
+// default) the first call on a device may also load the module and reserve the array on that device, so a
+// caller that must not see device memory taken makes one warm-up call first.  All calls share the array and
 // it keeps the contents of the last call, so the parts that must start at zero (queue counter,
 // accepted-term counters) are cleared on every call; two calls whose work overlaps on the GPU (other
 // streams, other contexts on the same device, other host threads) race on it and must be serialised
@@ -85,35 +87,38 @@ extern "C" int fp_rates4_noalloc(fp_ctx* c, int nT, const double* T, double sb, 
     return nfail(c, FP_EINVAL, "fp_rates4_noalloc: process_mask must be in [0, 7]");
   if (o.nu_select < 0 || o.nu_select > 2)
     return nfail(c, FP_EINVAL, "fp_rates4_noalloc: nu_select must be 0, 1 or 2");
+  if (o.no_time_reversal != 0 && o.no_time_reversal != 1)
+    return nfail(c, FP_EINVAL, "fp_rates4_noalloc: no_time_reversal must be 0 or 1");
   if (c->device < 0 || c->device >= kMaxDevices)
     return nfail(c, FP_EINVAL, "fp_rates4_noalloc: device ordinal too large");
   NA_CUDA(c, cudaSetDevice(c->device));
 
   // everything except the per-item partial sums has a fixed size; the partials get the rest, and the
   // plan enlarges the q' tile until they fit
-  fp::Plan p0;
   std::string err;
+  fp::Selection sel;
+  int rc = fp::make_selection(c, o, true, &sel, &err);
+  if (rc) return nfail(c, rc, "fp_rates4_noalloc: " + err);
+  fp::Plan p0;
   fp_rates_opts o_probe = o;
   if (o_probe.k1_tile <= 0) o_probe.k1_tile = c->N;  // smallest partials, for the fixed-size part
-  int rc = fp::plan_rates(c, o_probe, nT, 0, &p0, &err);
+  rc = fp::plan_rates(c, o_probe, nT, sel, 0, &p0, &err);
   if (rc) return nfail(c, rc, "fp_rates4_noalloc: " + err);
-  size_t sz[13], fixed = 0;
-  fp::scratch_sizes(c, p0, nT, o.mode_mask != nullptr, sz);
-  for (int i = 0; i < 13; ++i)
-    if (i != 4) fixed += sz[i];
-  if (fixed + sz[4] > kScratchBytes)
-    return nfail(c, FP_EINVAL, "fp_rates4_noalloc: this problem needs at least " + std::to_string(fixed + sz[4]) +
+  size_t sz[fp::kScratchParts], fixed = 0;
+  fp::scratch_sizes(c, p0, nT, sz);
+  for (int i = 0; i < fp::kScratchParts; ++i)
+    if (i != fp::kScratchPartial) fixed += sz[i];
+  if (fixed + sz[fp::kScratchPartial] > kScratchBytes)
+    return nfail(c, FP_EINVAL, "fp_rates4_noalloc: this problem needs at least " +
+                                   std::to_string(fixed + sz[fp::kScratchPartial]) +
                                    " bytes of scratch; the static scratch holds " + std::to_string(kScratchBytes) +
                                    " bytes (use fp_rates4_device)");
   fp::Plan p;
-  rc = fp::plan_rates(c, o, nT, kScratchBytes - fixed - 256, &p, &err);
+  rc = fp::plan_rates(c, o, nT, sel, kScratchBytes - fixed - 256, &p, &err);
   if (rc) return nfail(c, rc, "fp_rates4_noalloc: " + err);
-  fp::scratch_sizes(c, p, nT, o.mode_mask != nullptr, sz);
-  size_t total = 0, off[13];
-  for (int i = 0; i < 13; ++i) {
-    off[i] = total;
-    total += sz[i];
-  }
+  fp::scratch_sizes(c, p, nT, sz);
+  size_t total = 0;
+  for (size_t x : sz) total += x;
   if (total > kScratchBytes)
     return nfail(c, FP_EINVAL, "fp_rates4_noalloc: this problem needs " + std::to_string(total) +
                                    " bytes of scratch; the static scratch holds " + std::to_string(kScratchBytes) +
@@ -121,24 +126,11 @@ extern "C" int fp_rates4_noalloc(fp_ctx* c, int nT, const double* T, double sb, 
 
   unsigned char* b = nullptr;
   NA_CUDA(c, scratch_address(c->device, &b));
-  fp::Scratch sc;
-  sc.counters = reinterpret_cast<unsigned long long*>(b + off[0]);
-  sc.T = reinterpret_cast<double*>(b + off[1]);
-  sc.mask = o.mode_mask ? b + off[2] : nullptr;
-  sc.wt = reinterpret_cast<double*>(b + off[3]);
-  sc.partial = reinterpret_cast<double*>(b + off[4]);
-  sc.omh = reinterpret_cast<float*>(b + off[5]);
-  sc.oml = reinterpret_cast<float*>(b + off[6]);
-  sc.velh = reinterpret_cast<float*>(b + off[7]);
-  sc.vell = reinterpret_cast<float*>(b + off[8]);
-  sc.evf = reinterpret_cast<float2*>(b + off[9]);
-  sc.qfcf = reinterpret_cast<float*>(b + off[10]);
-  sc.twf = reinterpret_cast<float2*>(b + off[11]);
-  sc.wtf = reinterpret_cast<float*>(b + off[12]);
+  const fp::Scratch sc = fp::carve_scratch(b, sz);
   // run_rates clears the counters and the output on every call (the array keeps the last call's contents)
-  unsigned long long counts[4] = {0, 0, 0, 0};
-  rc = fp::run_rates(c, o, p, sc, nT, T, sb, d_out, counts, false, &err);
+  unsigned long long counts[fp::kCounters] = {0};
+  rc = fp::run_rates(c, o, sel, p, sc, nT, T, sb, d_out, counts, false, &err);
   if (rc) return nfail(c, rc, "fp_rates4_noalloc: " + err);
-  if (stats) fp::fill_stats(c, o, p, counts, stats);
+  if (stats) fp::fill_stats(c, o, sel, p, counts, stats);
   return FP_OK;
 }

@@ -56,21 +56,23 @@ __global__ void prep_kernel(RatesArgs a, float* omh, float* oml, float* velh, fl
   }
 }
 
-// rates[t][q][j] = pref * sum_tiles partial[(tile, q, chunk)][jj][t], in a fixed order.
+// rates[t][q][j] = pref * sum_tiles partial[(tile, qpos[q], chunk)][jj][t], in a fixed order, for every selected
+// mode of the output range (the others stay zero); under time reversal q and -q read the same partial sums.
 __global__ void reduce_kernel(RatesArgs a, double pref, double* rates) {
-  const long long n = (long long)a.nT * a.nq_sel * a.nb;
+  const long long n = (long long)a.nT * a.q_out_n * a.nb;
   long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= n) return;
   const int j = (int)(o % a.nb);
-  const int qi = (int)((o / a.nb) % a.nq_sel);
-  const int t = (int)(o / ((long long)a.nb * a.nq_sel));
+  const int q = a.q_out_begin + (int)((o / a.nb) % a.q_out_n);
+  const int t = (int)(o / ((long long)a.nb * a.q_out_n));
+  if (!a.sel[(size_t)q * a.nb + j]) return;
+  const int qi = a.qpos[q];
   const int chunk = j / a.J, jj = j % a.J;
   double s = 0.0;
   for (int tile = 0; tile < a.ntile; ++tile) {
     const long long item = ((long long)tile * a.nq_sel + qi) * a.nchunk + chunk;
     s += a.partial[((size_t)item * a.J + jj) * a.nT + t];
   }
-  const int q = a.q_begin + qi;
   rates[((size_t)t * a.N + q) * a.nb + j] = s * pref;
 }
 
@@ -98,13 +100,58 @@ size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 
-int plan_rates(fp_ctx* c, const fp_rates_opts& o, int nT, size_t partial_budget, Plan* p, std::string* err) {
+int make_selection(const fp_ctx* c, const fp_rates_opts& o, bool fold_allowed, Selection* s, std::string* err) {
   const int N = c->N, nb = c->nb;
   const int q_end = o.q_end <= 0 ? N : o.q_end;
   if (o.q_begin < 0 || o.q_begin > q_end || q_end > N) {
     *err = "bad q range";
     return FP_EINVAL;
   }
+  s->fold = fold_allowed && o.no_time_reversal == 0 && o.nu_select == 0;
+  s->q_out_begin = o.q_begin;
+  s->q_out_end = q_end;
+  const size_t nm = (size_t)N * nb;
+  s->sel.assign(nm, 0);
+  s->mult.assign(nm, 0);
+  s->qpos.assign(N, -1);
+  s->qlist.clear();
+  s->n_sel = 0;
+  s->n_exec = 0;
+  for (int q = o.q_begin; q < q_end; ++q)
+    for (int j = 0; j < nb; ++j) {
+      const size_t m = (size_t)q * nb + j;
+      s->sel[m] = (o.mode_mask == nullptr || o.mode_mask[m]) ? 1 : 0;
+      s->n_sel += s->sel[m];
+    }
+  // -q on the grid, componentwise (N_a - g_a) mod N_a
+  auto neg = [&](int q) {
+    const int g0 = q / (c->grid[1] * c->grid[2]), g1 = (q / c->grid[2]) % c->grid[1], g2 = q % c->grid[2];
+    const int m0 = (c->grid[0] - g0) % c->grid[0], m1 = (c->grid[1] - g1) % c->grid[1],
+              m2 = (c->grid[2] - g2) % c->grid[2];
+    return (m0 * c->grid[1] + m1) * c->grid[2] + m2;
+  };
+  for (int q = 0; q < N; ++q) {
+    const int p = s->fold ? neg(q) : q;
+    if (s->fold && p < q) continue;  // the pair {p, q} is evaluated at its smaller index p
+    int any = 0;
+    for (int j = 0; j < nb; ++j) {
+      int m = s->sel[(size_t)q * nb + j];
+      if (p != q) m += s->sel[(size_t)p * nb + j];
+      s->mult[(size_t)q * nb + j] = (unsigned char)m;
+      any |= m;
+      s->n_exec += m > 0 ? 1 : 0;
+    }
+    if (!any) continue;
+    s->qpos[q] = (int)s->qlist.size();
+    if (p != q) s->qpos[p] = (int)s->qlist.size();
+    s->qlist.push_back(q);
+  }
+  return FP_OK;
+}
+
+int plan_rates(fp_ctx* c, const fp_rates_opts& o, int nT, Selection& sel, size_t partial_budget, Plan* p,
+               std::string* err) {
+  const int N = c->N, nb = c->nb;
   if (!rates_kernel_ptr(o.precision, nb, nT)) {
     *err = "unsupported number of branches";
     return FP_EINVAL;
@@ -140,7 +187,7 @@ int plan_rates(fp_ctx* c, const fp_rates_opts& o, int nT, size_t partial_budget,
     *err = "threads must be a multiple of 32, >= block_j0*nb^2 and <= " + std::to_string(max_threads_for(nb));
     return FP_EINVAL;
   }
-  const int nq_sel = q_end - o.q_begin;
+  const int nq_sel = (int)sel.qlist.size();
   const int nchunk = nb / J;
   int t1 = o.k1_tile > 0 ? o.k1_tile : t1_tuned > 0 ? t1_tuned : (N + 511) / 512;
   auto part_bytes = [&](int tile) {
@@ -174,36 +221,70 @@ int plan_rates(fp_ctx* c, const fp_rates_opts& o, int nT, size_t partial_budget,
   p->nchunk = nchunk;
   p->ntile = (N + t1 - 1) / t1;
   p->nq_sel = nq_sel;
-  p->q_begin = o.q_begin;
-  p->q_end = q_end;
   p->n_items = (long long)p->ntile * nq_sel * nchunk;
   p->smem = smem;
   long long ctas = (long long)nsm * per_sm;
   if (ctas > p->n_items) ctas = p->n_items > 0 ? p->n_items : 1;
   p->ctas = (int)ctas;
+  sel.active_chunks = 0;
+  for (int q : sel.qlist)
+    for (int ch = 0; ch < nchunk; ++ch) {
+      int any = 0;
+      for (int jj = 0; jj < J; ++jj) any |= sel.mult[(size_t)q * nb + ch * J + jj];
+      sel.active_chunks += any ? 1 : 0;
+    }
   return FP_OK;
 }
 
-void scratch_sizes(const fp_ctx* c, const Plan& p, int nT, bool with_mask, size_t s[13]) {
+void scratch_sizes(const fp_ctx* c, const Plan& p, int nT, size_t s[kScratchParts]) {
   const size_t nm = (size_t)c->N * c->nb;
-  s[0] = up256(4 * sizeof(unsigned long long));
+  s[0] = up256(kCounters * sizeof(unsigned long long));
   s[1] = up256(kMaxT * sizeof(double));
-  s[2] = with_mask ? up256(nm) : 0;
-  s[3] = up256(3 * nm * nT * sizeof(double));
-  s[4] = up256((size_t)p.n_items * p.J * nT * sizeof(double));
-  s[5] = up256(nm * sizeof(float));
-  s[6] = up256(nm * sizeof(float));
-  s[7] = up256(3 * nm * sizeof(float));
-  s[8] = up256(3 * nm * sizeof(float));
-  s[9] = up256(nm * c->nb * sizeof(float2));
-  s[10] = up256((size_t)81 * c->nquart * sizeof(float));
-  s[11] = up256((size_t)c->L * sizeof(float2));
-  s[12] = up256(3 * nm * nT * sizeof(float));
+  s[2] = up256(nm);                                       // mult
+  s[3] = up256(nm);                                       // sel
+  s[4] = up256((size_t)c->N * sizeof(int));               // qlist
+  s[5] = up256((size_t)c->N * sizeof(int));               // qpos
+  s[6] = up256(3 * nm * nT * sizeof(double));             // wt
+  s[kScratchPartial] = up256((size_t)p.n_items * p.J * nT * sizeof(double));
+  s[8] = up256(nm * sizeof(float));
+  s[9] = up256(nm * sizeof(float));
+  s[10] = up256(3 * nm * sizeof(float));
+  s[11] = up256(3 * nm * sizeof(float));
+  s[12] = up256(nm * c->nb * sizeof(float2));
+  s[13] = up256((size_t)81 * c->nquart * sizeof(float));
+  s[14] = up256((size_t)c->L * sizeof(float2));
+  s[15] = up256(3 * nm * nT * sizeof(float));
 }
 
-int run_rates(fp_ctx* c, const fp_rates_opts& o, const Plan& p, const Scratch& sc, int nT, const double* T,
-              double sb, double* d_out, unsigned long long counts[4], bool use_graph, std::string* err,
-              int unit_stride) {
+Scratch carve_scratch(unsigned char* b, const size_t sz[kScratchParts]) {
+  size_t off[kScratchParts], acc = 0;
+  for (int i = 0; i < kScratchParts; ++i) {
+    off[i] = acc;
+    acc += sz[i];
+  }
+  Scratch sc;
+  sc.counters = reinterpret_cast<unsigned long long*>(b + off[0]);
+  sc.T = reinterpret_cast<double*>(b + off[1]);
+  sc.mult = b + off[2];
+  sc.sel = b + off[3];
+  sc.qlist = reinterpret_cast<int*>(b + off[4]);
+  sc.qpos = reinterpret_cast<int*>(b + off[5]);
+  sc.wt = reinterpret_cast<double*>(b + off[6]);
+  sc.partial = reinterpret_cast<double*>(b + off[kScratchPartial]);
+  sc.omh = reinterpret_cast<float*>(b + off[8]);
+  sc.oml = reinterpret_cast<float*>(b + off[9]);
+  sc.velh = reinterpret_cast<float*>(b + off[10]);
+  sc.vell = reinterpret_cast<float*>(b + off[11]);
+  sc.evf = reinterpret_cast<float2*>(b + off[12]);
+  sc.qfcf = reinterpret_cast<float*>(b + off[13]);
+  sc.twf = reinterpret_cast<float2*>(b + off[14]);
+  sc.wtf = reinterpret_cast<float*>(b + off[15]);
+  return sc;
+}
+
+int run_rates(fp_ctx* c, const fp_rates_opts& o, const Selection& sel, const Plan& p, const Scratch& sc, int nT,
+              const double* T, double sb, double* d_out, unsigned long long counts[kCounters], bool use_graph,
+              std::string* err, int unit_stride) {
   cudaStream_t s = c->stream;
   const int N = c->N, nb = c->nb;
   const size_t nm = (size_t)N * nb;
@@ -216,7 +297,11 @@ int run_rates(fp_ctx* c, const fp_rates_opts& o, const Plan& p, const Scratch& s
     }                                                                 \
   } while (0)
   RR_CUDA(cudaMemcpyAsync(sc.T, T, nT * sizeof(double), cudaMemcpyHostToDevice, s));
-  if (o.mode_mask) RR_CUDA(cudaMemcpyAsync(sc.mask, o.mode_mask, nm, cudaMemcpyHostToDevice, s));
+  RR_CUDA(cudaMemcpyAsync(sc.mult, sel.mult.data(), nm, cudaMemcpyHostToDevice, s));
+  RR_CUDA(cudaMemcpyAsync(sc.sel, sel.sel.data(), nm, cudaMemcpyHostToDevice, s));
+  RR_CUDA(cudaMemcpyAsync(sc.qpos, sel.qpos.data(), (size_t)N * sizeof(int), cudaMemcpyHostToDevice, s));
+  if (!sel.qlist.empty())
+    RR_CUDA(cudaMemcpyAsync(sc.qlist, sel.qlist.data(), sel.qlist.size() * sizeof(int), cudaMemcpyHostToDevice, s));
 
   RatesArgs a;
   std::memset(&a, 0, sizeof(a));  // padding included: the graph cache compares launch parameters bytewise
@@ -235,9 +320,14 @@ int run_rates(fp_ctx* c, const fp_rates_opts& o, const Plan& p, const Scratch& s
   a.t1 = p.t1;
   a.nchunk = p.nchunk;
   a.ntile = p.ntile;
-  a.q_begin = p.q_begin;
   a.nq_sel = p.nq_sel;
   a.n_items = p.n_items;
+  a.qlist = sc.qlist;
+  a.mult = sc.mult;
+  a.q_out_begin = sel.q_out_begin;
+  a.q_out_n = sel.q_out_end - sel.q_out_begin;
+  a.qpos = sc.qpos;
+  a.sel = sc.sel;
   a.omega = c->d_omega;
   a.evec = c->d_evec;
   a.vel = c->d_vel;
@@ -250,7 +340,6 @@ int run_rates(fp_ctx* c, const fp_rates_opts& o, const Plan& p, const Scratch& s
   a.kl_start = c->d_kl_start;
   a.kl_grp = c->d_kl_grp;
   a.tw = c->d_tw;
-  a.mask = o.mode_mask ? sc.mask : nullptr;
   a.omh = sc.omh;
   a.oml = sc.oml;
   a.velh = sc.velh;
@@ -295,13 +384,13 @@ int run_rates(fp_ctx* c, const fp_rates_opts& o, const Plan& p, const Scratch& s
     prep_kernel<<<4 * 152, 256, 0, s>>>(a, sc.omh, sc.oml, sc.velh, sc.vell, sc.evf, sc.qfcf, sc.twf, sc.wtf,
                                         want_f32);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(sc.counters, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(sc.counters, 0, kCounters * sizeof(unsigned long long), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(d_out, 0, (size_t)nT * nm * sizeof(double), s)) != cudaSuccess) return e;
     if (p.n_items > 0) {
       RatesArgs aa = a;
       void* args[] = {&aa};
       if ((e = cudaLaunchKernel(k, dim3(p.ctas), dim3(p.threads), args, p.smem, s)) != cudaSuccess) return e;
-      const long long n = (long long)nT * p.nq_sel * nb;
+      const long long n = (long long)nT * (sel.q_out_end - sel.q_out_begin) * nb;
       reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, pref, d_out);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -358,34 +447,31 @@ int run_rates(fp_ctx* c, const fp_rates_opts& o, const Plan& p, const Scratch& s
     RR_CUDA(enqueue());
   }
   RR_CUDA(cudaEventRecord(c->ev1, s));
-  RR_CUDA(cudaMemcpyAsync(counts, sc.counters, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  RR_CUDA(cudaMemcpyAsync(counts, sc.counters, kCounters * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   RR_CUDA(cudaStreamSynchronize(s));
 #undef RR_CUDA
   return FP_OK;
 }
 
-void fill_stats(const fp_ctx* c, const fp_rates_opts& o, const Plan& p, const unsigned long long counts[4],
-                fp_stats* st) {
+void fill_stats(const fp_ctx* c, const fp_rates_opts& o, const Selection& sel, const Plan& p,
+                const unsigned long long counts[kCounters], fp_stats* st) {
   const int N = c->N, nb = c->nb;
   std::memset(st, 0, sizeof(*st));
-  double nsel = 0;
-  if (o.mode_mask) {
-    for (int q = p.q_begin; q < p.q_end; ++q)
-      for (int j = 0; j < nb; ++j) nsel += o.mode_mask[(size_t)q * nb + j] ? 1 : 0;
-  } else {
-    nsel = (double)p.nq_sel * nb;
-  }
   const int pm = o.process_mask == 0 ? 7 : o.process_mask;
   const double nproc = (double)((pm & 1) + ((pm >> 1) & 1) + ((pm >> 2) & 1));
-  st->candidates = nproc * nsel * (double)N * (double)N * (double)nb * nb * nb;
+  const double per_mode = nproc * (double)N * (double)N * (double)nb * nb * nb;
+  st->candidates = per_mode * sel.n_sel;
+  st->candidates_executed = per_mode * sel.n_exec;
   for (int k = 0; k < 3; ++k) st->accepted[k] = (double)counts[1 + k];
-  // complex multiply-adds (8 flops each) of one rate set as scheduled: per item and q' the Psi prologue,
-  // per unordered (q', q'') pair the grouped assembly (9 J nb G), T (J nb^3 nb) and W (J nb^4)
+  st->vertex_entries = (double)counts[4];
+  st->terms_executed = (double)counts[5];
+  // complex multiply-adds (8 flops each) of the evaluated items: per item and q' the Psi prologue, per unordered
+  // (q', q'') pair the grouped assembly (9 J nb G) and T (J nb^3 nb), and nb per vertex entry W formed
   const double J = p.J;
   const double pairs = 0.5 * (double)N * (double)(N + 1);
-  const double per_pair = 8.0 * (9.0 * J * nb * c->G + 2.0 * J * (double)nb * nb * nb * nb);
+  const double per_pair = 8.0 * (9.0 * J * nb * c->G + J * (double)nb * nb * nb * nb);
   const double prolog = 8.0 * 9.0 * J * nb * 9.0 * c->nquart;
-  st->flops = (double)p.nq_sel * p.nchunk * (pairs * per_pair + (double)N * prolog);
+  st->flops = (double)sel.active_chunks * (pairs * per_pair + (double)N * prolog) + 8.0 * nb * st->vertex_entries;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, c->ev0, c->ev1);
   st->ms = ms;
@@ -403,42 +489,29 @@ int phase4_sampled(fp_ctx* c, int nT, const double* T, double sb, int stride, do
   fp_default_opts(&o);
   o.precision = FP_PREC_MIXED;
   o.no_graph = 1;
+  Selection sel;
+  int rc = make_selection(c, o, false, &sel, err);  // q' on a stride is not symmetric under q -> -q
+  if (rc) return rc;
   Plan p;
-  int rc = plan_rates(c, o, nT, 0, &p, err);
+  rc = plan_rates(c, o, nT, sel, 0, &p, err);
   if (rc) return rc;
   // a q' tile of one stride: every item owns exactly one sampled q'
   p.t1 = stride;
   p.ntile = (c->N + stride - 1) / stride;
   p.n_items = (long long)p.ntile * p.nq_sel * p.nchunk;
   if (p.ctas > p.n_items) p.ctas = (int)p.n_items;
-  size_t sz[13], total = 0, off[13];
-  scratch_sizes(c, p, nT, false, sz);
-  for (int i = 0; i < 13; ++i) {
-    off[i] = total;
-    total += sz[i];
-  }
+  size_t sz[kScratchParts], total = 0;
+  scratch_sizes(c, p, nT, sz);
+  for (size_t x : sz) total += x;
   unsigned char* b = nullptr;
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&b), total);
   if (e != cudaSuccess) {
     *err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
     return FP_ENOMEM;
   }
-  Scratch sc;
-  sc.counters = reinterpret_cast<unsigned long long*>(b + off[0]);
-  sc.T = reinterpret_cast<double*>(b + off[1]);
-  sc.mask = nullptr;
-  sc.wt = reinterpret_cast<double*>(b + off[3]);
-  sc.partial = reinterpret_cast<double*>(b + off[4]);
-  sc.omh = reinterpret_cast<float*>(b + off[5]);
-  sc.oml = reinterpret_cast<float*>(b + off[6]);
-  sc.velh = reinterpret_cast<float*>(b + off[7]);
-  sc.vell = reinterpret_cast<float*>(b + off[8]);
-  sc.evf = reinterpret_cast<float2*>(b + off[9]);
-  sc.qfcf = reinterpret_cast<float*>(b + off[10]);
-  sc.twf = reinterpret_cast<float2*>(b + off[11]);
-  sc.wtf = reinterpret_cast<float*>(b + off[12]);
-  unsigned long long counts[4];
-  rc = run_rates(c, o, p, sc, nT, T, sb, d_out, counts, false, err, stride);
+  Scratch sc = carve_scratch(b, sz);
+  unsigned long long counts[kCounters];
+  rc = run_rates(c, o, sel, p, sc, nT, T, sb, d_out, counts, false, err, stride);
   cudaFree(b);
   return rc;
 }

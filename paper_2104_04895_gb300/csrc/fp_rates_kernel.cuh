@@ -453,14 +453,16 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
   int* sKLg = sKLs + NA * NA + 1;    // [G]
   int* sQI = ib + cv.QI;             // [warp][kQCap]
   int* sEQ = ib + cv.EQ;             // [warp][kEQCap]
-  unsigned char* sMask = reinterpret_cast<unsigned char*>(ib + cv.nint);
+  // per j0 of the item: the selected modes the row stands for (0: inactive; 2: also written at -q)
+  unsigned char* sMult = reinterpret_cast<unsigned char*>(ib + cv.nint);
 
   // the row this thread owns in the contraction and screening phases
   const bool has_row = tid < rows;
   const int rjj = tid / NB2, rj1 = (tid / NB) % NB, rc = tid % NB;
   const size_t NM = (size_t)N * NB;
   const bool f32_sigma = !kF64 && a.dq_mode == 0;
-  unsigned long long cnt0 = 0, cnt1 = 0, cnt2 = 0;
+  // accepted terms (weighted by the rows' multiplicities), vertex entries formed, accepted terms evaluated
+  unsigned long long cnt0 = 0, cnt1 = 0, cnt2 = 0, nwf = 0, nte = 0;
   constexpr int S = acc_slots(NB);
   const int lane = tid & 31;
   const int qbase = (tid >> 5) * kQCap;
@@ -481,7 +483,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
     const long long rest = item / a.nchunk;
     const int qi = (int)(rest % a.nq_sel);
     const int tile = (int)(rest / a.nq_sel);
-    const int q = a.q_begin + qi;
+    const int q = a.qlist[qi];
     const int j0b = chunk * J;
     const int g[3] = {q / (a.grid[1] * a.grid[2]), (q / a.grid[2]) % a.grid[1], q % a.grid[2]};
 
@@ -492,7 +494,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
       sOm0[jj] = w;
       sHq[jj] = a.omh[m];
       sLq[jj] = a.oml[m];
-      sMask[jj] = (w > 0.0 && (a.mask == nullptr || a.mask[m])) ? 1 : 0;
+      sMult[jj] = w > 0.0 ? a.mult[m] : 0;
     }
     for (int o = tid; o < nT * J; o += nthr) {
       const int it = o / J, jj = o % J;
@@ -504,8 +506,9 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
     }
     __syncthreads();
     int any = 0;
-    for (int jj = 0; jj < J; ++jj) any |= sMask[jj];
-    const bool active = has_row && sMask[rjj];
+    for (int jj = 0; jj < J; ++jj) any |= sMult[jj];
+    const bool active = has_row && sMult[rjj] != 0;
+    const unsigned row_mult = active ? sMult[rjj] : 0u;
 
     double acc[S][MAXT];
     float acch[S][MAXT], accl[S][MAXT];
@@ -794,6 +797,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
             en -= count;
             double W2 = 1.0;
             if (ent && !unit) {
+              ++nwf;
               const int ej3 = (ent >> 6) & 15, ey = (ent >> 10) & 15, ex = (ent >> 14) & 15, ejq = ent >> 18;
               const C* tbe = sT + (size_t)(ejq * NB + ex) * (NB2 + 1) + ej3;
               const C* e2 = sE2 + ey * NB;
@@ -846,9 +850,10 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
               const float2 a0 = PA0[j3], a1 = PA1[j3], b0 = PB0[j3], b1 = PB1[j3];
               unsigned band = 0;
               FP_WINDOW_TEST()
-              cnt0 += __popc(accm & 0x09u);
-              cnt1 += __popc(accm & 0x12u);
-              cnt2 += __popc(accm & 0x24u);
+              cnt0 += row_mult * __popc(accm & 0x09u);
+              cnt1 += row_mult * __popc(accm & 0x12u);
+              cnt2 += row_mult * __popc(accm & 0x24u);
+              nte += __popc(accm);
             }
             // entries with an accepted candidate, one per lane at most, in lane order
             const unsigned bal = __ballot_sync(0xffffffffu, accm != 0);
@@ -907,8 +912,13 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
                 unsigned accm = 0, band = 0;
                 FP_WINDOW_TEST()
                 if (!accm) continue;
+                cnt0 += row_mult * __popc(accm & 0x09u);
+                cnt1 += row_mult * __popc(accm & 0x12u);
+                cnt2 += row_mult * __popc(accm & 0x24u);
+                nte += __popc(accm);
                 C Wv = cmk<R>(unit ? 1 : 0, 0);
                 if (!unit) {
+                  ++nwf;
 #pragma unroll
                   for (int c = 0; c < NB; ++c) cfma(Wv, e2row[c], tb[c * NB + j3]);
                 }
@@ -917,9 +927,6 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
                   const int c = __ffs(accm) - 1;
                   accm &= accm - 1;
                   const int p = c % 3;
-                  cnt0 += (p == 0);
-                  cnt1 += (p == 1);
-                  cnt2 += (p == 2);
                   const bool ordA = c < 3;
                   const int tab = (c < 3) ? (c == 0 ? 0 : 1) : (c == 3 ? 2 : 3);
                   const int ent = tab * NB2 + (ordA ? y : x) * NB + j3;
@@ -1005,16 +1012,20 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
     }
     __syncthreads();
   }
-  // accepted counts
+  // accepted counts and vertex entries formed
   for (int off = 16; off > 0; off >>= 1) {
     cnt0 += __shfl_down_sync(0xffffffffu, cnt0, off);
     cnt1 += __shfl_down_sync(0xffffffffu, cnt1, off);
     cnt2 += __shfl_down_sync(0xffffffffu, cnt2, off);
+    nwf += __shfl_down_sync(0xffffffffu, nwf, off);
+    nte += __shfl_down_sync(0xffffffffu, nte, off);
   }
   if ((tid & 31) == 0) {
     if (cnt0) atomicAdd(a.counts + 0, cnt0);
     if (cnt1) atomicAdd(a.counts + 1, cnt1);
     if (cnt2) atomicAdd(a.counts + 2, cnt2);
+    if (nwf) atomicAdd(a.counts + 3, nwf);
+    if (nte) atomicAdd(a.counts + 4, nte);
   }
 }
 

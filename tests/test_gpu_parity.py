@@ -285,3 +285,46 @@ def test_normal_and_umklapp_match_the_oracle(lib, maker):
         total += acc
     assert np.array_equal(np.array(st["accepted"]), total)
     assert np.array_equal(umk, nu[:, 1])
+
+
+def _neg_index(grid, q):
+    g = np.unravel_index(q, grid)
+    return int(np.ravel_multi_index(tuple((-np.asarray(g)) % np.asarray(grid)), grid))
+
+
+@pytest.mark.parametrize("maker", [lambda: synth.diamond_si((3, 3, 2)), lambda: synth.zincblende_bas((4, 3, 3)),
+                                   lambda: synth.licoo2((2, 2, 2)), lambda: synth.simple_cubic((4, 4, 4))],
+                         ids=["diamond-3x3x2", "bas-4x3x3", "licoo2-2x2x2", "sc-4x4x4"])
+def test_time_reversal_evaluates_half_the_grid(lib, maker):
+    """The default path evaluates one point of each pair {q, -q} (e^{-lambda} = conj e^{lambda}, Sec. 2.2) and
+    writes its rates at both; every q evaluated separately (no_time_reversal = 1) and the oracle agree with it,
+    accepted counts are exact integers, and the screened candidates drop to (N + self-conjugate points) / 2N."""
+    cr = maker()
+    w, e, v = oracle_modes(cr)
+    temps = [300.0, 800.0]
+    ref, acc = oracle.rates4(cr, w, e, v, temps=temps)
+    with lib.Context.from_crystal(cr) as ctx:
+        ctx.set_modes(w, e, v)
+        fold, st_f = ctx.rates4(temps, cr.scalebroad)
+        every, st_e = ctx.rates4(temps, cr.scalebroad, no_time_reversal=1)
+        fold_m, st_fm = ctx.rates4(temps, cr.scalebroad, precision=FP_PREC_MIXED)
+        with pytest.raises(lib.FourPhononError):
+            ctx.rates4(temps, cr.scalebroad, no_time_reversal=2)
+    nT = len(temps)
+    compare(fold.reshape(nT, -1), ref, RTOL_FP64)
+    compare(every.reshape(nT, -1), ref, RTOL_FP64)
+    compare(fold_m.reshape(nT, -1), ref, RTOL_MIXED)
+    for st in (st_f, st_e, st_fm):
+        assert np.array_equal(np.array(st["accepted"]), acc)
+        assert st["candidates"] == 3 * cr.nq ** 3 * cr.nb ** 4
+    N = cr.nq
+    selfconj = sum(1 for q in range(N) if _neg_index(cr.grid, q) == q)
+    assert st_e["candidates_executed"] == st_e["candidates"]
+    assert st_f["candidates_executed"] == st_f["candidates"] * (N + selfconj) / (2 * N)
+    if selfconj < N:  # on a grid of 2s every point is its own -q and nothing folds
+        assert st_f["vertex_entries"] < st_e["vertex_entries"] and st_f["flops"] < st_e["flops"]
+        assert st_f["terms_executed"] < st_e["terms_executed"]
+    else:
+        assert st_f["vertex_entries"] == st_e["vertex_entries"]
+    for q in range(N):
+        assert np.array_equal(fold[:, q], fold[:, _neg_index(cr.grid, q)])
