@@ -29,7 +29,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2104_04895_gb300 import synth  # noqa: E402
-from paper_2104_04895_gb300.sharding import max_over_ranks, shard  # noqa: E402
+from paper_2104_04895_gb300.sharding import (balanced_shard, estimate_costs, load_imbalance,  # noqa: E402
+                                              max_over_ranks, rank_mask)
 
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (recipe nominal; 152 SMs x 2070 MHz x 2 DFMA/clk/SM x 2 = 1.26)
 FP32_PEAK_TFLOPS = 80.5   # 152 SMs x 2070 MHz x 128 FFMA/clk/SM x 2
@@ -52,8 +53,11 @@ def parse():
     p.add_argument("--surrogate", action="store_true", help="learned-rate study instead of the bench line")
     p.add_argument("--configs", action="store_true",
                    help="per-workload study: time and oracle error of both precisions on workloads 1-5")
-    p.add_argument("--budget-s", type=float, default=60.0,
-                   help="--configs: per-precision time budget; larger rate sets are timed on a q-range")
+    p.add_argument("--budget-s", type=float, default=300.0,
+                   help="per-workload records: a precision whose full rate set is estimated above this many seconds "
+                        "is timed on strided q-slices and extrapolated")
+    p.add_argument("--no-configs", action="store_true",
+                   help="leave out the per-workload records (simple cubic 4^3, BAs 12^3, LiCoO2, diamond 16^3)")
     p.add_argument("--seed", type=int, default=2104)
     p.add_argument("--grid", type=int, nargs=3, default=None,
                    help="override the workload's q-grid (small profiling cases only; not a bench line)")
@@ -124,6 +128,20 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def e2e_input_bytes(binding, cr):
+    """Bytes a step hands the library from host memory: the buffers passed to fp_init (lattice, positions,
+    masses, the packed Phi2 and Phi4 lists), fp_set_fc3 (packed Phi3) and fp_rates4 (temperatures), measured from
+    the objects themselves."""
+    import ctypes
+    n = np.ascontiguousarray(cr.lattice, np.float64).nbytes + np.ascontiguousarray(cr.frac, np.float64).nbytes
+    n += np.ascontiguousarray(cr.mass, np.float64).nbytes + 8 * len(cr.temps)
+    n += ctypes.sizeof(binding.pack_fc2(cr.fc2_idx, cr.fc2_val)) + ctypes.sizeof(binding.pack_fc4(cr.fc4_idx,
+                                                                                                  cr.fc4_val))
+    if cr.fc3_idx is not None:
+        n += len(cr.fc3_idx) * ctypes.sizeof(binding.fp_fc3)
+    return int(n)
+
+
 def cpu_baseline(cr, seconds, w=None, e=None, v=None):
     """FP64 oracle on sampled modes with full partner sums, until about `seconds` of CPU work."""
     import oracle
@@ -181,10 +199,11 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def time_precision(ctx, binding, torch, cr, prec, q0, q1, out, flush, stream, steps, warmup, barrier, clk=None):
-    """Time `steps` full rate sets (after `warmup`) with CUDA events on the library's stream."""
+def time_precision(ctx, binding, torch, cr, prec, part, out, flush, stream, steps, warmup, barrier, clk=None):
+    """Time `steps` full rate sets (after `warmup`) with CUDA events on the library's stream; `part` holds this
+    rank's rate options (its mode mask under a multi-GPU partition)."""
     def step():
-        return ctx.rates4_device(cr.temps, out.data_ptr(), cr.scalebroad, precision=prec, q_begin=q0, q_end=q1)
+        return ctx.rates4_device(cr.temps, out.data_ptr(), cr.scalebroad, precision=prec, **part)
 
     for _ in range(warmup):
         st = step()
@@ -229,7 +248,6 @@ def main():
     if args.grid:
         cr = cr.with_grid(args.grid)
     N, nb, nT = cr.nq, cr.nb, len(cr.temps)
-    q0, q1 = shard(N, ws, rank)
 
     def barrier():
         if ws > 1:
@@ -248,7 +266,16 @@ def main():
 
     cands_step = 3.0 * N * N * N * nb ** 4          # all ranks together: one full-grid rate set per step
     clk = ClockSampler(local)
-    total_ms, kms, st = time_precision(ctx, binding, torch, cr, main_prec, q0, q1, out, flush, stream, args.steps,
+    # this rank's q-points: all of them on one GPU; on several, the pairs {q, -q} dealt by estimated cost (every
+    # rank computes the same integer counts, hence the same partition, with no communication)
+    part, part_desc = {}, "one GPU, whole grid"
+    if ws > 1:
+        costs = estimate_costs(ctx, cr.temps, cr.scalebroad)
+        parts = balanced_shard(costs, cr.grid, ws)
+        part = {"mode_mask": rank_mask(parts[rank], N, nb)}
+        part_desc = (f"pairs {{q, -q}} dealt by estimated cost over {ws} GPUs, estimated max/mean "
+                     f"{load_imbalance(costs, parts, cr.grid):.3f}")
+    total_ms, kms, st = time_precision(ctx, binding, torch, cr, main_prec, part, out, flush, stream, args.steps,
                                        args.warmup, barrier, clk)
     total_ms = max_over_ranks(total_ms, dist if ws > 1 else None, dev)
     value = cands_step * args.steps / (total_ms * 1e-3)
@@ -259,7 +286,7 @@ def main():
     peak = FP64_PEAK_TFLOPS if main_prec == binding.FP_PREC_FP64 else FP32_PEAK_TFLOPS
     other = None
     if not args.no_other:
-        o_ms, o_kms, o_st = time_precision(ctx, binding, torch, cr, other_prec, q0, q1, out_other, flush, stream,
+        o_ms, o_kms, o_st = time_precision(ctx, binding, torch, cr, other_prec, part, out_other, flush, stream,
                                            args.steps, args.warmup, barrier)
         o_ms = max_over_ranks(o_ms, dist if ws > 1 else None, dev)
         o_peak = FP64_PEAK_TFLOPS if other_prec == binding.FP_PREC_FP64 else FP32_PEAK_TFLOPS
@@ -275,8 +302,8 @@ def main():
     # three-phonon rates of the same workload (FP64, one launch after a warm-up launch), for context
     three = None
     if not args.no_other and cr.fc3_idx is not None:
-        ctx.rates3(cr.temps, cr.scalebroad, q_begin=q0, q_end=q1)
-        _, st3 = ctx.rates3(cr.temps, cr.scalebroad, q_begin=q0, q_end=q1)
+        ctx.rates3(cr.temps, cr.scalebroad, **part)
+        _, st3 = ctx.rates3(cr.temps, cr.scalebroad, **part)
         s3 = max_over_ranks(st3["ms"], dist if ws > 1 else None, dev) * 1e-3
         three = {"precision": "fp64", "s_per_rate_set": s3, "candidates": st3["candidates"],
                  "terms_per_s": st3["candidates"] / s3, "accepted": st3["accepted"][:2]}
@@ -290,15 +317,20 @@ def main():
         t0 = time.perf_counter()
         with binding.Context.from_crystal(cr, device=local) as c2:
             c2.modes(copy=False)
-            r, _ = c2.rates4(cr.temps, cr.scalebroad, precision=main_prec, q_begin=q0, q_end=q1, **(tuned or {}))
+            r, _ = c2.rates4(cr.temps, cr.scalebroad, precision=main_prec, **part, **(tuned or {}))
         t1 = time.perf_counter()
         if i > 0:
             e2e_times.append(t1 - t0)
-        h2d = 8 * (9 + cr.natoms * 4 + len(cr.temps)) + 96 * len(cr.fc2_idx) + 704 * len(cr.fc4_idx)
+        h2d = e2e_input_bytes(binding, cr)
         d2h = r.nbytes
     e2e_s = float(np.mean(e2e_times)) if e2e_times else float("nan")
     e2e_s = max_over_ranks(e2e_s, dist if ws > 1 else None, dev)
     e2e_value = cands_step / e2e_s
+
+    # the other benchmark workloads, one record each (rank 0 of a single-GPU run)
+    configs = None
+    if ws == 1 and not args.no_configs and not args.grid:
+        configs = [measure_workload(binding, wl, full_fp64_max_s=args.budget_s) for wl in (1, 3, 4, 5)]
 
     if rank == 0:
         base = None
@@ -326,7 +358,7 @@ def main():
                        "time_reversal": "one q of each pair {q, -q} evaluated, rates written at both",
                        "l2": "flushed between timed steps (256 MB write)", "tile": st["tile"],
                        "autotuned_mixed_tile": tuned,
-                       "parallelism": f"q-partition over {ws} GPU(s)"},
+                       "parallelism": part_desc},
             "rel_err_vs_oracle_sampled": rel_err,
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved_tflops / peak, "traffic": None,
@@ -335,6 +367,7 @@ def main():
                          "flops_vertex": st["flops"], "flops_accumulate": acc_flops},
             "other_precision": other,
             "three_phonon": three,
+            "configs": configs,
             "cpu_baseline": base,
             "e2e": {"value": e2e_value, "unit": "process-terms/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "s_per_rate_set": e2e_s},
@@ -381,54 +414,100 @@ def run_surrogate(args):
     print(json.dumps(line), flush=True)
 
 
-def run_configs(args):
-    """One JSON line per workload: seconds per full-grid rate set (measured, or extrapolated from a timed
-    q-range when a full set would exceed the budget), process-terms/s and the oracle error on sampled modes."""
+def _self_conjugate(grid):
+    """Number of grid points q with -q = q (mod the grid)."""
+    n = 1
+    for g in grid:
+        n *= 2 if g % 2 == 0 else 1
+    return n
+
+
+def _slice_mask(cr, m, k):
+    """All branches of the q-points q = k (mod m): a strided slice that spreads over the whole grid."""
+    mask = np.zeros((cr.nq, cr.nb), np.uint8)
+    mask[k::m] = 1
+    return mask.reshape(-1)
+
+
+def measure_workload(binding, wl, budget_slice_s=20.0, full_fp64_max_s=300.0, oracle_max_s=150.0):
+    """Seconds per full-grid rate set of workload `wl` in both precisions, and errors on sampled modes.
+
+    A precision whose full rate set is estimated (from a one-q probe) to stay under `full_fp64_max_s` is timed on
+    the whole grid.  Otherwise three strided q-slices (q = k mod m, all branches) are timed and scaled to the grid
+    by the candidates the kernel screened (time reversal evaluates (N + self-conjugate points) / 2 points of a full
+    grid); the spread of the three gives the sampling uncertainty.  The GPU takes the oracle's modes, so the error
+    against the oracle on a ruled mode sample (lowest positive frequency and one seeded mode) is a strict one; the
+    oracle runs only where it finishes within `oracle_max_s` on the host cores."""
     import oracle
+    import oracle.modes as om
+    cr = synth.workload(wl)
+    N, nb, nT = cr.nq, cr.nb, len(cr.temps)
+    cands = 3.0 * N ** 3 * nb ** 4
+    full_exec = 3.0 * N * N * nb ** 3 * nb * (N + _self_conjugate(cr.grid)) / 2.0
+    w, e, v = om.modes(cr)
+    flat = w.reshape(-1)
+    pos = np.nonzero(flat > 0)[0]
+    rng = np.random.Generator(np.random.PCG64(77 + wl))
+    sample = [int(pos[np.argmin(flat[pos])]), int(rng.choice(pos))]
+    if N * nb > 5000:
+        sample = sample[:1]  # the oracle takes a minute or more per mode here
+    res = {"workload": synth.WORKLOAD_NAMES[wl], "candidates": cands, "temperatures": nT,
+           "sample_modes": sample}
+    outs = {}
+    with binding.Context.from_crystal(cr) as ctx:
+        ctx.set_modes(w, e, v)
+        for name, prec in (("fp64", binding.FP_PREC_FP64), ("mixed", binding.FP_PREC_MIXED)):
+            probe = np.zeros(N * nb, np.uint8)
+            probe[nb:2 * nb] = 1                                   # q = 1, all branches (also warms the kernel)
+            _, st = ctx.rates4(cr.temps, cr.scalebroad, precision=prec, mode_mask=probe, no_graph=1)
+            t_rep = st["ms"] * 1e-3 * nb * 3.0 * N * N * nb ** 3 / st["candidates_executed"]
+            est = t_rep * full_exec / (nb * 3.0 * N * N * nb ** 3)
+            smask = np.zeros(N * nb, np.uint8)
+            smask[sample] = 1
+            if est <= full_fp64_max_s:
+                out, st = ctx.rates4(cr.temps, cr.scalebroad, precision=prec)
+                secs = st["ms"] * 1e-3
+                rec = {"s_per_rate_set": secs, "terms_per_s": cands / secs, "timing": "full grid, one rate set",
+                       "accepted": st["accepted"], "candidates_executed": st["candidates_executed"]}
+                outs[name] = out.reshape(nT, -1)[:, sample]
+            else:
+                m = max(2, int(np.ceil(N * t_rep / budget_slice_s)))
+                ext = []
+                for k in (0, m // 3, (2 * m) // 3):
+                    _, st = ctx.rates4(cr.temps, cr.scalebroad, precision=prec, mode_mask=_slice_mask(cr, m, k),
+                                       no_graph=1)
+                    ext.append(st["ms"] * 1e-3 * full_exec / st["candidates_executed"])
+                secs = float(np.mean(ext))
+                rec = {"s_per_rate_set": secs, "terms_per_s": cands / secs,
+                       "timing": f"extrapolated from three strided q-slices (q = k mod {m}, k = 0, {m // 3}, "
+                                 f"{(2 * m) // 3}) by screened candidates",
+                       "slice_spread": float((max(ext) - min(ext)) / secs)}
+                out, _ = ctx.rates4(cr.temps, cr.scalebroad, precision=prec, mode_mask=smask, no_graph=1)
+                outs[name] = out.reshape(nT, -1)[:, sample]
+            rec["tile"] = st["tile"]
+            res[name] = rec
+    res["mixed"]["rel_err_vs_fp64_gpu"] = float(np.max(np.abs(outs["mixed"] - outs["fp64"]) / outs["fp64"]))
+    # oracle cost per mode on these host cores: about 3 N^2 nb^3 terms at 1.6e7 (6 / nb)^3 terms/s on 16 cores
+    cores = os.cpu_count() or 1
+    t_or = 3.0 * N ** 2 * nb ** 3 / (1.6e7 * (6.0 / nb) ** 3 * cores / 16.0)
+    if t_or * len(sample) <= oracle_max_s:
+        t0 = time.perf_counter()
+        ref, _ = oracle.rates4(cr, w, e, v, sel=sample, nthreads=cores)
+        dt = time.perf_counter() - t0
+        res["oracle"] = {"s_per_mode": dt / len(sample), "terms_per_s": 3.0 * N ** 2 * nb ** 3 * len(sample) / dt,
+                         "cores": cores}
+        for name in ("fp64", "mixed"):
+            res[name]["rel_err_vs_oracle"] = float(np.max(np.abs(outs[name] - ref) / ref))
+    else:
+        res["oracle"] = {"skipped": f"about {t_or:.0f} s per mode on {cores} cores"}
+    return res
+
+
+def run_configs(args):
+    """One JSON line per workload (see measure_workload)."""
     from paper_2104_04895_gb300 import binding
     for wl in (1, 2, 3, 4, 5):
-        cr = synth.workload(wl)
-        N, nb = cr.nq, cr.nb
-        cands = 3.0 * N ** 3 * nb ** 4
-        res = {"workload": synth.WORKLOAD_NAMES[wl], "candidates": cands}
-        with binding.Context.from_crystal(cr) as ctx:
-            w, e, v = ctx.modes()
-            ctx.autotune(cr.temps, cr.scalebroad, precision=binding.FP_PREC_MIXED)
-            rng = np.random.Generator(np.random.PCG64(77 + wl))
-            sel = [int(m) for m in rng.choice(np.arange(nb, N * nb), size=1, replace=False)]
-            q_s = sel[0] // nb
-            ref = None
-            # the oracle's cost per mode on 16 Arm cores, measured: 3 N^2 nb^3 terms at ~1.6e7 (6 / nb)^3
-            # terms/s (its vertex grows as nb^6 per q-pair); skip it beyond ~2.5 minutes
-            if 3.0 * N ** 2 * nb ** 3 / (1.6e7 * (6.0 / nb) ** 3) <= 150.0:
-                t0 = time.perf_counter()
-                ref, _ = oracle.rates4(cr, w, e, v, sel=sel, nthreads=os.cpu_count() or 1)
-                t_or = time.perf_counter() - t0
-                res["oracle"] = {"s_per_mode": t_or, "terms_per_s": 3.0 * N ** 2 * nb ** 3 / t_or,
-                                 "cores": os.cpu_count()}
-            vals = {}
-            for name, prec in (("fp64", binding.FP_PREC_FP64), ("mixed", binding.FP_PREC_MIXED)):
-                # probe a q-range to decide between a full run and an extrapolated one
-                nq_probe = max(1, min(N, N // 64))
-                _, st = ctx.rates4(cr.temps, cr.scalebroad, precision=prec, q_begin=0, q_end=nq_probe)
-                est = st["ms"] * 1e-3 * N / nq_probe
-                if est <= args.budget_s:
-                    out, st = ctx.rates4(cr.temps, cr.scalebroad, precision=prec)
-                    secs, how = st["ms"] * 1e-3, "full grid"
-                    val = out.reshape(len(cr.temps), -1)[:, sel]
-                else:
-                    nq = max(1, int(N * args.budget_s / est / 2))
-                    q0 = min(max(0, q_s - nq // 2), N - nq)
-                    out, st = ctx.rates4(cr.temps, cr.scalebroad, precision=prec, q_begin=q0, q_end=q0 + nq)
-                    secs, how = st["ms"] * 1e-3 * N / nq, f"extrapolated from q-range of {nq}/{N} points"
-                    val = out.reshape(len(cr.temps), -1)[:, sel]
-                vals[name] = val
-                err = float(np.max(np.abs(val - ref) / np.abs(ref))) if ref is not None else None
-                res[name] = {"s_per_rate_set": secs, "terms_per_s": cands / secs, "timing": how,
-                             "rel_err_vs_oracle": err, "tile": st["tile"]}
-            res["mixed"]["rel_err_vs_fp64_gpu"] = float(np.max(np.abs(vals["mixed"] - vals["fp64"]) /
-                                                             np.abs(vals["fp64"])))
-        print(json.dumps(res), flush=True)
+        print(json.dumps(measure_workload(binding, wl, full_fp64_max_s=args.budget_s)), flush=True)
 
 
 if __name__ == "__main__":

@@ -83,6 +83,11 @@ typedef struct {
                                       evaluation at -q gives; accepted counts are exact); 1: evaluate every
                                       selected q.  The normal/Umklapp split (nu_select != 0) evaluates every q,
                                       because a zone-boundary tie breaks the symmetry of the representatives. */
+  int tensor_cores;                /* 1: in the mixed precision with nb = 6, the per-q'' contraction T = A conj(E3)
+                                      of Eq. V4's vertex runs on the fifth-generation tensor cores (tcgen05 kind::tf32
+                                      in split precision, A = A_hi + A_lo and E = E_hi + E_lo in tf32, three
+                                      products, FP32 accumulation in tensor memory); 0 (default): CUDA cores.
+                                      FP_EINVAL for other precisions or branch counts. */
 } fp_rates_opts;
 
 /* Counters of one fp_rates4 call. */
@@ -207,6 +212,23 @@ int fp_phase3(fp_ctx* ctx, int nT, const double* T, double scalebroad, const fp_
 int fp_phase4(fp_ctx* ctx, int nT, const double* T, double scalebroad, int stride, double* wp4);
 
 /*
+ * Four-phonon phase space of every mode: the paper's onlyharmonic task with four_phonon on (Sec. 2.1), whose
+ * outputs are BTE.Numprocess_4ph, BTE.P4 and BTE.WP4 (Appendix A).  The sums are those of fp_rates4 with |V4|^2
+ * replaced by 1 and without hbar^2 pi / 8 (Eqs. tao0 and 4phgamma without V4), over q' on a stride (stride 1 =
+ * the full sums; stride s uses every s-th q' with all q'' and scales by s):
+ *   numprocess[m] = number of accepted process terms (q', q'', branch triple, process) of mode m (host, N x nb);
+ *   p4[m]         = (1/N^2) sum c_p delta_p                                                (host, N x nb; ps);
+ *   wp4[t][m]     = (1/N^2) sum c_p B_p/n delta_p / (w w' w'' w''')                        (host, nT x N x nb).
+ * The paper prints no formula for P4 and WP4 (it cites them); these are the rate's sum with the vertex, and for
+ * P4 also the Bose and frequency factors, set to 1.  Window, Gaussian, small-sigma rule, multiplicities c_p and
+ * time reversal (stride 1) as in fp_rates4; opts: precision (FP64 default), window, sigma_min, dq_mode,
+ * mode_mask, q range, process_mask and nu_select apply.  Any output may be NULL.  Two kernel passes (unit weights,
+ * then Bose weights).  Requires modes (FP_ESTATE otherwise); FP_EINVAL for stride outside [1, N].
+ */
+int fp_phase_space4(fp_ctx* ctx, int nT, const double* T, double scalebroad, const fp_rates_opts* opts, int stride,
+                    double* numprocess, double* p4, double* wp4);
+
+/*
  * Channel-resolved rates: the ++ (recombination), +- (redistribution) and -- (splitting) parts of Eq.
  * 4phgamma, whose sum is fp_rates4's rate.  rates: host, nT x 3 x N x nb, channel index in the order ++, +-,
  * --.  opts->process_mask must be 0.  Each channel is one rate-kernel pass (the vertex is recomputed), so
@@ -225,6 +247,27 @@ typedef struct {
   int Rj[3], Rk[3];
   double fc[27];
 } fp_fc3;
+
+/*
+ * Force-constant files (host only; no GPU is touched).  The paper's program reads the fourth-order force
+ * constants from FORCE_CONSTANTS_4TH beside the third-order FORCE_CONSTANTS_3RD (Appendix A) and does not print
+ * the layout.  These calls use the block layout of ShengBTE's third-order file, extended by one atom:
+ *   <number of blocks> <blank> then per block: <block number, 1-based>; one line "x y z" per partner atom with
+ *   the Cartesian position (A) of that atom's cell (n . A, A the lattice rows); the 1-based atom indices;
+ *   3^order lines "alpha beta gamma [theta] value" (1-based Cartesian indices, eV/A^3 or eV/A^4); <blank>.
+ * The first atom lies in the home cell.  Values are written with 17 significant digits, so writing and reading
+ * back returns every value bit for bit.  Positions are read back as the nearest lattice vector, which must
+ * reproduce them within 1e-6 A (FP_EINVAL otherwise).
+ *   fp_write_fc4 / fp_write_fc3: write n blocks (fp_fc4 / fp_fc3, atom indices 0-based) to `path`.
+ *   fp_read_fc4 / fp_read_fc3: *n receives the number of blocks in `path`; with out != NULL and cap >= *n the
+ *   blocks are stored in out (0-based atom indices, cells in lattice coordinates).  out = NULL only counts.
+ * Errors: FP_EINVAL (unreadable or malformed file, a position that is not a lattice vector, cap too small);
+ * the message is in fp_last_error(NULL).
+ */
+int fp_write_fc4(const char* path, const double lattice[9], int n, const fp_fc4* fc4);
+int fp_read_fc4(const char* path, const double lattice[9], fp_fc4* out, int cap, int* n);
+int fp_write_fc3(const char* path, const double lattice[9], int n, const fp_fc3* fc3);
+int fp_read_fc3(const char* path, const double lattice[9], fp_fc3* out, int cap, int* n);
 
 /* Store (replace) the third-order force constants of the context.  The library copies them. */
 int fp_set_fc3(fp_ctx* ctx, int n_fc3, const fp_fc3* fc3);
@@ -301,8 +344,9 @@ int fp_mlp_loss_grad(int device, int n_in, int batch, const float* X, const floa
 
 /* Options of fp_surrogate_fit; zero fields are not defaults: start from fp_surrogate_default_opts. */
 typedef struct {
-  double train_frac;       /* share of positive-frequency modes with exact training rates (0.10) */
-  double holdout_frac;     /* share of modes with exact rates that only judge the network (0.05) */
+  double train_frac;       /* share of the pairs {q, -q} whose positive-frequency modes get exact training
+                              rates (0.10); whole pairs, because the rate path evaluates a pair at once */
+  double holdout_frac;     /* share of the pairs whose exact rates only judge the network (0.05) */
   double tol;              /* held-out relative error bound above which a bin falls back to exact rates (0.05) */
   unsigned long long seed; /* seeds the mode subsets, the initial weights and the minibatch order */
   int epochs;              /* Adam epochs (400) */

@@ -93,6 +93,9 @@ def rates4(cryst, omega, evec, vel, temps=None, scalebroad=None, window=2.0, sig
            sel=None, unit_vertex=False, nthreads=0, processes=(0, 1, 2), nu=None):
     """Rates (nT, nsel) in ps^-1 and accepted counts (3,) for modes sel (default: all).
 
+    unit_vertex: False/0 the rates; True/1 |V|^2 := 1 (weighted phase space WP4, sum without prefactor and 1/N^2);
+    2 also Bose and frequency factors := 1 (phase space P4: sum of c_p delta_p).
+
     processes: the classes of Eq. 4phgamma summed, 0 ++ (recombination), 1 +- (redistribution), 2 --
     (splitting); the default sums all three (the full rate).  nu: None (all), "normal" or "umklapp" (Sec. 2.2,
     Q = 0 or not; the reading is in fp_oracle.c at orc_bz_shift)."""
@@ -120,7 +123,7 @@ def rates4(cryst, omega, evec, vel, temps=None, scalebroad=None, window=2.0, sig
     acc_p = acc.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     rc = lib().oracle_rates4(grid_p, lat_p, cryst.natoms, m_p, len(qi), qi_p, qf_p, om_p, ev_p, ve_p,
                              len(T), T_p, float(sb), float(window), float(sigma_min), int(dq_mode),
-                             len(sel_a), sel_p, int(bool(unit_vertex)), sum(1 << int(p) for p in set(processes)),
+                             len(sel_a), sel_p, int(unit_vertex), sum(1 << int(p) for p in set(processes)),
                              nu_select, int(nthreads), out_p, acc_p)
     if rc != 0:
         raise ValueError("oracle_rates4 rejected its arguments")

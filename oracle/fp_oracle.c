@@ -279,7 +279,9 @@ static const double ORC_MULT[3] = {0.5, 0.5, 1.0 / 6.0};
  * Four-phonon RTA rates of selected modes.
  *   sel[s] = q * nb + j (mode id); rates[t * nsel + s] in ps^-1.
  *   accepted[3]: number of terms that passed the energy window, per process, over the selected modes.
- *   unit_vertex != 0 replaces |V|^2 by 1 (the weighted phase space of the same processes).
+ *   unit_vertex: 0 the rates; 1 replaces |V|^2 by 1 (the weighted phase space WP4 of the same processes); 2 also
+ *   replaces B_p / n_lambda / (w w' w'' w''') by 1 (the phase space P4: sum of c_p delta_p).  With 1 or 2 the sum
+ *   is returned without the prefactor hbar^2 pi / (8 N^2) and without the 1/N^2.
  *   proc_mask selects the process classes summed in Eq. 4phgamma: bit 0 ++ (recombination), bit 1 +-
  *   (redistribution), bit 2 -- (splitting); 7 gives the full rate.
  *   nu_select: 0 all processes, 1 normal ones only, 2 Umklapp ones only (orc_is_umklapp).
@@ -369,7 +371,10 @@ int oracle_rates4(const int grid[3], const double lattice[9], int natoms, const 
                       B = (1.0 + n1) * n2 * n3;
                     else
                       B = n1 * n2 * n3;
-                    part[(size_t)q1 * nT + it] += ORC_MULT[pr] * B / n0 * v2 * delta / (w * w1 * w2 * w3);
+                    if (unit_vertex == 2)
+                      part[(size_t)q1 * nT + it] += ORC_MULT[pr] * delta;
+                    else
+                      part[(size_t)q1 * nT + it] += ORC_MULT[pr] * B / n0 * v2 * delta / (w * w1 * w2 * w3);
                   }
                 }
               }

@@ -43,7 +43,8 @@ class fp_rates_opts(ctypes.Structure):
                 ("dq_mode", ctypes.c_int), ("mode_mask", ctypes.POINTER(ctypes.c_ubyte)),
                 ("q_begin", ctypes.c_int), ("q_end", ctypes.c_int), ("block_j0", ctypes.c_int),
                 ("k1_tile", ctypes.c_int), ("threads", ctypes.c_int), ("no_graph", ctypes.c_int),
-                ("process_mask", ctypes.c_int), ("nu_select", ctypes.c_int), ("no_time_reversal", ctypes.c_int)]
+                ("process_mask", ctypes.c_int), ("nu_select", ctypes.c_int), ("no_time_reversal", ctypes.c_int),
+                ("tensor_cores", ctypes.c_int)]
 
 
 class fp_stats(ctypes.Structure):
@@ -60,7 +61,7 @@ class fp_stats(ctypes.Structure):
 EXPORTS = ["fp_version", "fp_default_opts", "fp_init", "fp_set_stream", "fp_modes", "fp_set_modes", "fp_rates4",
            "fp_rates4_channels", "fp_rates4_nu", "fp_set_fc3", "fp_rates3", "fp_kappa_rta", "fp_rates4_irreducible", "fp_star_table", "fp_rates4_device", "fp_rates4_noalloc", "fp_autotune", "fp_phase3", "fp_phase4", "fp_mlp_params_size",
            "fp_mlp_loss_grad", "fp_surrogate_default_opts", "fp_surrogate_fit", "fp_surrogate_rates", "fp_free",
-           "fp_last_error"]
+           "fp_last_error", "fp_phase_space4", "fp_write_fc4", "fp_read_fc4", "fp_write_fc3", "fp_read_fc3"]
 
 
 class fp_surrogate_opts(ctypes.Structure):
@@ -159,6 +160,18 @@ def load(path: str | None = None):
     L.fp_surrogate_fit.restype = ctypes.c_int
     L.fp_surrogate_rates.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_ubyte)]
     L.fp_surrogate_rates.restype = ctypes.c_int
+    L.fp_phase_space4.argtypes = [vp, ctypes.c_int, dp, ctypes.c_double, ctypes.POINTER(fp_rates_opts), ctypes.c_int,
+                                  dp, dp, dp]
+    L.fp_phase_space4.restype = ctypes.c_int
+    cp = ctypes.c_char_p
+    L.fp_write_fc4.argtypes = [cp, dp, ctypes.c_int, ctypes.POINTER(fp_fc4)]
+    L.fp_write_fc4.restype = ctypes.c_int
+    L.fp_read_fc4.argtypes = [cp, dp, ctypes.POINTER(fp_fc4), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L.fp_read_fc4.restype = ctypes.c_int
+    L.fp_write_fc3.argtypes = [cp, dp, ctypes.c_int, ctypes.POINTER(fp_fc3)]
+    L.fp_write_fc3.restype = ctypes.c_int
+    L.fp_read_fc3.argtypes = [cp, dp, ctypes.POINTER(fp_fc3), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L.fp_read_fc3.restype = ctypes.c_int
     L.fp_free.argtypes = [vp]
     L.fp_free.restype = None
     L.fp_last_error.argtypes = [vp]
@@ -184,6 +197,17 @@ def pack_fc2(idx, val):
         for d in range(3):
             arr[b].Rj[d] = int(ix[2 + d])
         ctypes.memmove(arr[b].fc, np.ascontiguousarray(v, np.float64).ctypes.data, 72)
+    return arr
+
+
+def pack_fc3(idx, val):
+    arr = (fp_fc3 * max(1, len(idx)))()
+    for b, (ix, v) in enumerate(zip(idx, val)):
+        arr[b].i, arr[b].j, arr[b].k = (int(x) for x in ix[:3])
+        for d in range(3):
+            arr[b].Rj[d] = int(ix[3 + d])
+            arr[b].Rk[d] = int(ix[6 + d])
+        ctypes.memmove(arr[b].fc, np.ascontiguousarray(v, np.float64).ctypes.data, 216)
     return arr
 
 
@@ -229,14 +253,19 @@ class Context:
     def set_fc3(self, idx, val):
         """fp_set_fc3: triplets idx (n3, 9) = i, j, k, Rj[3], Rk[3] and values (n3, 27) in eV/A^3."""
         idx = np.asarray(idx)
-        val = np.asarray(val, np.float64)
-        arr = (fp_fc3 * max(1, len(idx)))()
-        for n, (ix, v) in enumerate(zip(idx, val)):
-            arr[n].i, arr[n].j, arr[n].k = int(ix[0]), int(ix[1]), int(ix[2])
-            for d in range(3):
-                arr[n].Rj[d], arr[n].Rk[d] = int(ix[3 + d]), int(ix[6 + d])
-            arr[n].fc[:] = [float(x) for x in v]
-        _check(self.L, self.h, self.L.fp_set_fc3(self.h, len(idx), arr))
+        _check(self.L, self.h, self.L.fp_set_fc3(self.h, len(idx), pack_fc3(idx, np.asarray(val, np.float64))))
+
+    def phase_space4(self, temps, scalebroad=1.0, stride=1, **opts):
+        """fp_phase_space4: (numprocess (N*nb), p4 (N*nb), wp4 (nT, N*nb)), the onlyharmonic outputs."""
+        T = np.ascontiguousarray(temps, np.float64).reshape(-1)
+        o, keep = self.make_opts(**opts)
+        npr = np.zeros(self.N * self.nb)
+        p4 = np.zeros(self.N * self.nb)
+        wp4 = np.zeros((len(T), self.N * self.nb))
+        _check(self.L, self.h, self.L.fp_phase_space4(self.h, len(T), _dp(T), float(scalebroad), ctypes.byref(o),
+                                                      int(stride), _dp(npr), _dp(p4), _dp(wp4)))
+        del keep
+        return npr, p4, wp4
 
     def kappa_rta(self, temps, rates):
         """fp_kappa_rta: kappa (nT, 3, 3) in W/(m K) from rates (nT, N, nb) in ps^-1."""
@@ -300,7 +329,7 @@ class Context:
     @staticmethod
     def make_opts(precision=FP_PREC_FP64, window=2.0, sigma_min=1e-10, dq_mode=0, mode_mask=None, q_begin=0,
                   q_end=0, block_j0=0, k1_tile=0, threads=0, no_graph=0, process_mask=0, nu_select=0,
-                  no_time_reversal=0):
+                  no_time_reversal=0, tensor_cores=0):
         o = fp_rates_opts()
         o.precision, o.window, o.sigma_min, o.dq_mode = int(precision), float(window), float(sigma_min), int(dq_mode)
         o.q_begin, o.q_end, o.block_j0, o.k1_tile, o.threads = int(q_begin), int(q_end), int(block_j0), \
@@ -309,6 +338,7 @@ class Context:
         o.process_mask = int(process_mask)
         o.nu_select = int(nu_select)
         o.no_time_reversal = int(no_time_reversal)
+        o.tensor_cores = int(tensor_cores)
         keep = None
         if mode_mask is not None:
             keep = np.ascontiguousarray(mode_mask, np.uint8)
@@ -456,3 +486,47 @@ def star_table(grid, ops):
     if rc != FP_OK:
         raise FourPhononError(rc, "fp_star_table rejected the operations")
     return rep, n.value
+
+
+def _lat(lattice):
+    return np.ascontiguousarray(lattice, np.float64).reshape(9)
+
+
+def write_fc4(path, lattice, idx, val):
+    """fp_write_fc4: quartets idx (n, 13) = i, j, k, l, Rj[3], Rk[3], Rl[3] (0-based atoms), val (n, 81) eV/A^4."""
+    L = load()
+    lat = _lat(lattice)
+    _check(L, None, L.fp_write_fc4(os.fsencode(path), _dp(lat), len(idx), pack_fc4(idx, val)))
+
+
+def read_fc4(path, lattice):
+    """fp_read_fc4: (idx (n, 13) int32, val (n, 81)) in the layout of write_fc4."""
+    L = load()
+    lat = _lat(lattice)
+    n = ctypes.c_int(0)
+    _check(L, None, L.fp_read_fc4(os.fsencode(path), _dp(lat), None, 0, ctypes.byref(n)))
+    arr = (fp_fc4 * max(1, n.value))()
+    _check(L, None, L.fp_read_fc4(os.fsencode(path), _dp(lat), arr, n.value, ctypes.byref(n)))
+    idx = np.array([[a.i, a.j, a.k, a.l, *a.Rj, *a.Rk, *a.Rl] for a in arr[:n.value]], np.int32).reshape(-1, 13)
+    val = np.array([list(a.fc) for a in arr[:n.value]], np.float64).reshape(-1, 81)
+    return idx, val
+
+
+def write_fc3(path, lattice, idx, val):
+    """fp_write_fc3: triplets idx (n, 9) = i, j, k, Rj[3], Rk[3] (0-based atoms), val (n, 27) eV/A^3."""
+    L = load()
+    lat = _lat(lattice)
+    _check(L, None, L.fp_write_fc3(os.fsencode(path), _dp(lat), len(idx), pack_fc3(idx, val)))
+
+
+def read_fc3(path, lattice):
+    """fp_read_fc3: (idx (n, 9) int32, val (n, 27)) in the layout of write_fc3."""
+    L = load()
+    lat = _lat(lattice)
+    n = ctypes.c_int(0)
+    _check(L, None, L.fp_read_fc3(os.fsencode(path), _dp(lat), None, 0, ctypes.byref(n)))
+    arr = (fp_fc3 * max(1, n.value))()
+    _check(L, None, L.fp_read_fc3(os.fsencode(path), _dp(lat), arr, n.value, ctypes.byref(n)))
+    idx = np.array([[a.i, a.j, a.k, *a.Rj, *a.Rk] for a in arr[:n.value]], np.int32).reshape(-1, 9)
+    val = np.array([list(a.fc) for a in arr[:n.value]], np.float64).reshape(-1, 27)
+    return idx, val

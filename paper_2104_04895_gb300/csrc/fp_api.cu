@@ -102,6 +102,10 @@ int neg_index(const fp_ctx* c, int q) {
 
 }  // namespace
 
+namespace fp {
+int fail_global(int code, const std::string& msg) { return fail(nullptr, code, msg); }
+}  // namespace fp
+
 extern "C" {
 
 int fp_version(void) { return 10000; }
@@ -418,6 +422,7 @@ static int validate_opts(fp_ctx* c, int nT, const double* T, double sb, const fp
   if (o->nu_select < 0 || o->nu_select > 2) return fail(c, FP_EINVAL, "fp_rates4: nu_select must be 0, 1 or 2");
   if (o->no_time_reversal != 0 && o->no_time_reversal != 1)
     return fail(c, FP_EINVAL, "fp_rates4: no_time_reversal must be 0 or 1");
+  if (o->tensor_cores != 0 && o->tensor_cores != 1) return fail(c, FP_EINVAL, "fp_rates4: tensor_cores must be 0 or 1");
   return FP_OK;
 }
 
@@ -633,3 +638,76 @@ int fp_rates4_nu(fp_ctx* c, int nT, const double* T, double scalebroad, const fp
 
 }  // extern "C"
 
+
+namespace {
+
+// one unit-vertex pass (|W|^2 := 1) of the rate kernel over q' on a stride; d_out nT x N x nb, d_counts N x nb
+int phase_pass(fp_ctx* c, const fp_rates_opts& o, int nT, const double* T, double sb, int stride, bool unit_weights,
+               double* d_out, double* d_counts, std::string* err) {
+  fp::Selection sel;
+  int rc = fp::make_selection(c, o, stride == 1, &sel, err);  // a q' stride is not symmetric under q -> -q
+  if (rc) return rc;
+  fp::Plan p;
+  rc = fp::plan_rates(c, o, nT, sel, 0, &p, err);
+  if (rc) return rc;
+  if (stride > 1) {  // a q' tile of one stride: every item owns exactly one sampled q'
+    p.t1 = stride;
+    p.ntile = (c->N + stride - 1) / stride;
+    p.n_items = (long long)p.ntile * p.nq_sel * p.nchunk;
+    if (p.ctas > p.n_items) p.ctas = (int)std::max<long long>(1, p.n_items);
+  }
+  size_t sz[fp::kScratchParts], total = 0;
+  fp::scratch_sizes(c, p, nT, sz);
+  for (size_t x : sz) total += x;
+  const size_t cnt_bytes = (size_t)std::max<long long>(1, p.n_items) * p.J * sizeof(unsigned long long);
+  unsigned char* b = nullptr;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&b), total + cnt_bytes);
+  if (e != cudaSuccess) {
+    *err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    return FP_ENOMEM;
+  }
+  const fp::Scratch sc = fp::carve_scratch(b, sz);
+  fp::RunExtra x;
+  x.unit_stride = stride;
+  x.unit_weights = unit_weights;
+  x.d_item_counts = reinterpret_cast<unsigned long long*>(b + total);
+  x.d_mode_counts = d_counts;
+  unsigned long long counts[fp::kCounters];
+  rc = fp::run_rates(c, o, sel, p, sc, nT, T, sb, d_out, counts, false, err, x);
+  cudaFree(b);
+  return rc;
+}
+
+}  // namespace
+
+extern "C" int fp_phase_space4(fp_ctx* c, int nT, const double* T, double scalebroad, const fp_rates_opts* opts,
+                               int stride, double* numprocess, double* p4, double* wp4) {
+  if (!c) return fail(nullptr, FP_EINVAL, "fp_phase_space4: NULL context");
+  fp_rates_opts o;
+  int rc = validate_opts(c, nT, T, scalebroad, opts, &o);
+  if (rc) return rc;
+  if (stride < 1 || stride > c->N) return fail(c, FP_EINVAL, "fp_phase_space4: stride must be in [1, N]");
+  o.no_graph = 1;
+  FP_CUDA(c, cudaSetDevice(c->device));
+  const size_t nm = (size_t)c->N * c->nb;
+  double* d = nullptr;
+  FP_CUDA(c, dalloc(&d, nm * (2 + (size_t)nT) + nm));
+  double* d_p4 = d;
+  double* d_cnt = d + nm;
+  double* d_wp4 = d + 2 * nm;
+  double* d_cnt2 = d + (2 + (size_t)nT) * nm;
+  std::string err;
+  // pass 1: unit weights (P4) and the accepted terms per mode; pass 2: Bose and frequency weights (WP4)
+  rc = phase_pass(c, o, 1, T, scalebroad, stride, true, d_p4, d_cnt, &err);
+  if (!rc && wp4) rc = phase_pass(c, o, nT, T, scalebroad, stride, false, d_wp4, d_cnt2, &err);
+  cudaError_t e = cudaSuccess;
+  if (!rc && numprocess) e = cudaMemcpyAsync(numprocess, d_cnt, nm * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (!rc && e == cudaSuccess && p4) e = cudaMemcpyAsync(p4, d_p4, nm * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (!rc && e == cudaSuccess && wp4)
+    e = cudaMemcpyAsync(wp4, d_wp4, nT * nm * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(d);
+  if (rc) return fail(c, rc, "fp_phase_space4: " + err);
+  if (e != cudaSuccess) return fail(c, FP_ECUDA, std::string("fp_phase_space4: ") + cudaGetErrorString(e));
+  return FP_OK;
+}

@@ -65,13 +65,16 @@ struct RatesArgs {
   double rec[9];
   double* partial;           // [n_items][J][nT]
   unsigned long long* counter;
-  unsigned long long* counts; // [5]: accepted ++, +-, -- (weighted by mult), vertex entries W formed, accepted
-                              // terms evaluated
+  unsigned long long* counts; // [6]: accepted ++, +-, -- (weighted by mult), vertex entries W formed, accepted
+                              // terms evaluated, tensor-core completion waits that ran out of polls
   int unit_vertex;           // 1: |W|^2 = 1 (weighted phase space), q' on a stride, ordered (q', q'') pairs
   int k1_stride;             // q' stride of the unit-vertex mode
   unsigned cand_mask;        // candidates summed (bit c = ordering * 3 + process), from process_mask
   int nu_select;             // 0: all processes, 1: normal only, 2: Umklapp only
   const int* bzm;            // [N][3] Brillouin-zone shifts of the grid points (normal/Umklapp reading)
+  unsigned long long* item_counts;  // [n_items][J] accepted terms per (item, j0), or null (not counted)
+  double* mode_counts;       // [N*nb] reduction output: accepted terms per selected mode x count_scale, or null
+  double count_scale;
 };
 
 // Which q-points a rates call evaluates, and for which modes.  Time reversal (e^{-lambda} = conj e^{lambda},
@@ -100,7 +103,7 @@ struct Plan {
 // Device working memory of one rates call (owned by the caller of run_rates), in the order of scratch_sizes.
 constexpr int kScratchParts = 16;
 constexpr int kScratchPartial = 7;  // index of the per-item partial sums
-constexpr int kCounters = 8;        // queue, accepted ++, +-, --, vertex entries, terms evaluated, spare
+constexpr int kCounters = 8;        // queue, accepted ++, +-, --, vertex entries, terms evaluated, wait timeouts, spare
 struct Scratch {
   unsigned long long* counters;  // [kCounters]
   double* T;                     // [kMaxT]
@@ -198,17 +201,26 @@ int plan_rates(fp_ctx* c, const fp_rates_opts& o, int nT, Selection& sel, size_t
 void scratch_sizes(const fp_ctx* c, const Plan& p, int nT, size_t sizes[kScratchParts]);
 // Scratch pointers laid out from `base` with the sizes of scratch_sizes.
 Scratch carve_scratch(unsigned char* base, const size_t sizes[kScratchParts]);
+// Variants of a rates launch used by the phase-space entry points.
+struct RunExtra {
+  int unit_stride = 0;          // > 0: |W|^2 := 1, q' on this stride, ordered (q', q'') pairs, no prefactor
+  bool unit_weights = false;    // Bose and frequency weights := 1 (the unweighted phase space)
+  unsigned long long* d_item_counts = nullptr;  // [n_items][J]: with d_mode_counts, per-mode accepted terms
+  double* d_mode_counts = nullptr;              // [N*nb] accepted terms of each selected mode x unit_stride
+};
 // Upload the selection, enqueue weights, FP32 prep, the persistent rate kernel and the reduction on c->stream,
 // then wait and return the counters.  d_out: nT x N x nb doubles (zeroed here).
 // use_graph: capture the device part once per set of launch parameters and replay it as a CUDA graph.
 int run_rates(fp_ctx* c, const fp_rates_opts& o, const Selection& sel, const Plan& p, const Scratch& s, int nT,
               const double* T, double sb, double* d_out, unsigned long long counts[kCounters], bool use_graph,
-              std::string* err, int unit_stride = 0);
+              std::string* err, const RunExtra& x = RunExtra());
 // Sampled four-phonon weighted phase space of every mode (surrogate feature): the rate sum with |W|^2 = 1
 // over q' on a stride (ordered pairs), scaled to the full grid; d_out: nT x N x nb, mixed precision.
 int phase4_sampled(fp_ctx* c, int nT, const double* T, double sb, int stride, double* d_out, std::string* err);
 // Brillouin-zone shifts of the grid points (fp_sym.cu), N x 3
 void bz_shifts(const int grid[3], const double rec[9], int* out);
+// Record a message for fp_last_error(NULL) (calls without a context) and return code.
+int fail_global(int code, const std::string& msg);
 void fill_stats(const fp_ctx* c, const fp_rates_opts& o, const Selection& sel, const Plan& p,
                 const unsigned long long counts[kCounters], fp_stats* st);
 }  // namespace fp

@@ -89,6 +89,8 @@ extern "C" int fp_rates4_noalloc(fp_ctx* c, int nT, const double* T, double sb, 
     return nfail(c, FP_EINVAL, "fp_rates4_noalloc: nu_select must be 0, 1 or 2");
   if (o.no_time_reversal != 0 && o.no_time_reversal != 1)
     return nfail(c, FP_EINVAL, "fp_rates4_noalloc: no_time_reversal must be 0 or 1");
+  if (o.tensor_cores != 0 && o.tensor_cores != 1)
+    return nfail(c, FP_EINVAL, "fp_rates4_noalloc: tensor_cores must be 0 or 1");
   if (c->device < 0 || c->device >= kMaxDevices)
     return nfail(c, FP_EINVAL, "fp_rates4_noalloc: device ordinal too large");
   NA_CUDA(c, cudaSetDevice(c->device));

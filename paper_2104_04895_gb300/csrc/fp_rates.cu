@@ -7,6 +7,7 @@ namespace fp {
 // kernel pointers of the two precision instantiations (fp_rates_f64.cu, fp_rates_f32.cu)
 const void* rates_kernel_f64(int nb, int maxt);
 const void* rates_kernel_f32(int nb, int maxt);
+const void* rates_kernel_f32_tc(int nb, int maxt);
 
 namespace {
 
@@ -74,21 +75,37 @@ __global__ void reduce_kernel(RatesArgs a, double pref, double* rates) {
     s += a.partial[((size_t)item * a.J + jj) * a.nT + t];
   }
   rates[((size_t)t * a.N + q) * a.nb + j] = s * pref;
+  if (a.mode_counts && t == 0) {
+    unsigned long long cnt = 0;
+    for (int tile = 0; tile < a.ntile; ++tile) {
+      const long long item = ((long long)tile * a.nq_sel + qi) * a.nchunk + chunk;
+      cnt += a.item_counts[(size_t)item * a.J + jj];
+    }
+    a.mode_counts[(size_t)q * a.nb + j] = (double)cnt * a.count_scale;
+  }
 }
 
-// kernel for (precision, nb, number of temperatures): one accumulator per temperature, 1 or up to 8
-const void* rates_kernel_ptr(int precision, int nb, int nT) {
+// p[i] = v (the unit weight table of the unweighted phase space)
+__global__ void fill_kernel(double* p, long long n, double v) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+// kernel for (precision, nb, number of temperatures, tensor cores): one accumulator per temperature, 1 or up to 8
+const void* rates_kernel_ptr(int precision, int nb, int nT, bool tc) {
   const int maxt = nT == 1 ? 1 : kMaxT;
+  if (tc) return precision == FP_PREC_MIXED ? rates_kernel_f32_tc(nb, maxt) : nullptr;
   return precision == FP_PREC_FP64 ? rates_kernel_f64(nb, maxt) : rates_kernel_f32(nb, maxt);
 }
 
-size_t smem_bytes(int precision, int nb, int J, int G, int nquart, int nT, int threads) {
+size_t smem_bytes(int precision, int nb, int J, int G, int nquart, int nT, int threads, bool tc) {
   Carve c = make_carve(nb, J, G, nquart, nT, threads, precision != FP_PREC_FP64);
-  return c.bytes(precision == FP_PREC_FP64 ? sizeof(Cx<double>) : sizeof(Cx<float>));
+  const size_t b = c.bytes(precision == FP_PREC_FP64 ? sizeof(Cx<double>) : sizeof(Cx<float>));
+  return tc ? align128(b) + kTcBytes : b;
 }
 
-int max_ctas_per_sm(int precision, int nb, int nT, int threads, size_t smem) {
-  const void* k = rates_kernel_ptr(precision, nb, nT);
+int max_ctas_per_sm(int precision, int nb, int nT, int threads, size_t smem, bool tc) {
+  const void* k = rates_kernel_ptr(precision, nb, nT, tc);
   if (!k) return 0;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   int n = 0;
@@ -152,7 +169,12 @@ int make_selection(const fp_ctx* c, const fp_rates_opts& o, bool fold_allowed, S
 int plan_rates(fp_ctx* c, const fp_rates_opts& o, int nT, Selection& sel, size_t partial_budget, Plan* p,
                std::string* err) {
   const int N = c->N, nb = c->nb;
-  if (!rates_kernel_ptr(o.precision, nb, nT)) {
+  const bool tc = o.tensor_cores != 0;
+  if (tc && (o.precision != FP_PREC_MIXED || nb != 6)) {
+    *err = "tensor_cores needs the mixed precision and 6 branches";
+    return FP_EINVAL;
+  }
+  if (!rates_kernel_ptr(o.precision, nb, nT, tc)) {
     *err = "unsupported number of branches";
     return FP_EINVAL;
   }
@@ -170,7 +192,7 @@ int plan_rates(fp_ctx* c, const fp_rates_opts& o, int nT, Selection& sel, size_t
     // largest divisor of nb whose rows fit a block and whose tile leaves room for two blocks per SM
     J = nb;
     while (J > 1 && (J * nb * nb > max_threads_for(nb) ||
-                     smem_bytes(o.precision, nb, J, c->G, c->nquart, nT, max_threads_for(nb)) > 110 * 1024)) {
+                     smem_bytes(o.precision, nb, J, c->G, c->nquart, nT, max_threads_for(nb), tc) > 110 * 1024)) {
       int nj = J - 1;
       while (nj > 1 && nb % nj) --nj;
       J = nj;
@@ -200,12 +222,12 @@ int plan_rates(fp_ctx* c, const fp_rates_opts& o, int nT, Selection& sel, size_t
     *err = "per-item partial sums do not fit the scratch";
     return FP_EINVAL;
   }
-  const size_t smem = smem_bytes(o.precision, nb, J, c->G, c->nquart, nT, threads);
+  const size_t smem = smem_bytes(o.precision, nb, J, c->G, c->nquart, nT, threads, tc);
   if (smem > 227 * 1024) {
     *err = "tile does not fit in shared memory";
     return FP_EINVAL;
   }
-  const int per_sm = max_ctas_per_sm(o.precision, nb, nT, threads, smem);
+  const int per_sm = max_ctas_per_sm(o.precision, nb, nT, threads, smem, tc);
   if (per_sm < 1) {
     *err = "kernel tile cannot be resident on an SM";
     return FP_EINVAL;
@@ -284,7 +306,8 @@ Scratch carve_scratch(unsigned char* b, const size_t sz[kScratchParts]) {
 
 int run_rates(fp_ctx* c, const fp_rates_opts& o, const Selection& sel, const Plan& p, const Scratch& sc, int nT,
               const double* T, double sb, double* d_out, unsigned long long counts[kCounters], bool use_graph,
-              std::string* err, int unit_stride) {
+              std::string* err, const RunExtra& x) {
+  const int unit_stride = x.unit_stride;
   cudaStream_t s = c->stream;
   const int N = c->N, nb = c->nb;
   const size_t nm = (size_t)N * nb;
@@ -368,6 +391,9 @@ int run_rates(fp_ctx* c, const fp_rates_opts& o, const Selection& sel, const Pla
   }
   a.nu_select = o.nu_select;
   a.bzm = c->d_bzm;
+  a.item_counts = x.d_mode_counts ? x.d_item_counts : nullptr;
+  a.mode_counts = x.d_mode_counts;
+  a.count_scale = unit_stride > 0 ? (double)unit_stride : 1.0;
 
   const int want_f32 = o.precision != FP_PREC_FP64;
   const double conv = kConv;
@@ -375,12 +401,21 @@ int run_rates(fp_ctx* c, const fp_rates_opts& o, const Selection& sel, const Pla
   const double pref = unit_stride > 0
                           ? (double)unit_stride / ((double)N * (double)N)
                           : kPi * kHbar * kHbar * conv * conv * conv * conv / (8.0 * (double)N * (double)N);
-  const void* k = rates_kernel_ptr(o.precision, nb, nT);
+  const void* k = rates_kernel_ptr(o.precision, nb, nT, o.tensor_cores != 0);
   // the device part of a rate set: Bose weights, FP32 tables, cleared counters and output, the persistent
   // rate kernel and the reduction
   auto enqueue = [&]() -> cudaError_t {
-    cudaError_t e = launch_weights(c, nT, sc.T, sc.wt, s);
+    cudaError_t e = cudaSuccess;
+    if (x.unit_weights) {
+      fill_kernel<<<152, 256, 0, s>>>(sc.wt, 3LL * (long long)nm * nT, 1.0);
+      e = cudaGetLastError();
+    } else {
+      e = launch_weights(c, nT, sc.T, sc.wt, s);
+    }
     if (e != cudaSuccess) return e;
+    if (x.d_mode_counts &&
+        (e = cudaMemsetAsync(x.d_mode_counts, 0, nm * sizeof(double), s)) != cudaSuccess)
+      return e;
     prep_kernel<<<4 * 152, 256, 0, s>>>(a, sc.omh, sc.oml, sc.velh, sc.vell, sc.evf, sc.qfcf, sc.twf, sc.wtf,
                                         want_f32);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -450,6 +485,10 @@ int run_rates(fp_ctx* c, const fp_rates_opts& o, const Selection& sel, const Pla
   RR_CUDA(cudaMemcpyAsync(counts, sc.counters, kCounters * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   RR_CUDA(cudaStreamSynchronize(s));
 #undef RR_CUDA
+  if (counts[6] != 0) {
+    *err = "a tensor-core completion wait ran out of polls (" + std::to_string(counts[6]) + " warps); results invalid";
+    return FP_ECUDA;
+  }
   return FP_OK;
 }
 
@@ -511,7 +550,9 @@ int phase4_sampled(fp_ctx* c, int nT, const double* T, double sb, int stride, do
   }
   Scratch sc = carve_scratch(b, sz);
   unsigned long long counts[kCounters];
-  rc = run_rates(c, o, sel, p, sc, nT, T, sb, d_out, counts, false, err, stride);
+  RunExtra x;
+  x.unit_stride = stride;
+  rc = run_rates(c, o, sel, p, sc, nT, T, sb, d_out, counts, false, err, x);
   cudaFree(b);
   return rc;
 }

@@ -13,4 +13,10 @@ const void* rates_kernel_f32(int nb, int maxt) {
     default: return nullptr;
   }
 }
+// the tensor-core T contraction (nb = 6 only)
+const void* rates_kernel_f32_tc(int nb, int maxt) {
+  if (nb != 6) return nullptr;
+  return maxt == 1 ? reinterpret_cast<const void*>(rates_kernel<float, 6, 1, true>)
+                   : reinterpret_cast<const void*>(rates_kernel<float, 6, kMaxT, true>);
+}
 }  // namespace fp

@@ -38,6 +38,7 @@
 #include <cstring>
 
 #include "fp_internal.cuh"
+#include "fp_tc.cuh"
 
 namespace fp {
 namespace {
@@ -148,7 +149,7 @@ struct Carve {
   size_t Hq, Lq, H1, L1, H2, L2, H3, L3, VH1, VL1, VH2, VL2, VH3, VL3, Sigf, F0, F1, F2, F3, nflt;  // floats
   size_t KL, QI, EQ, nint;                                                        // ints
   size_t Mask;                                                                // bytes
-  size_t bytes(size_t cx_size) const {
+  __host__ __device__ size_t bytes(size_t cx_size) const {
     return ncx * cx_size + ndbl * sizeof(double) + nflt * sizeof(float) + nint * sizeof(int) + Mask + 16;
   }
 };
@@ -300,6 +301,17 @@ __device__ __forceinline__ double dw_fp64(int c, double w0, double wx, double wy
   return __dsub_rn(t2, w3);
 }
 
+// Tensor-core variant of the mixed path (nb = 6): shared-memory region after the carve, 128-byte aligned.
+// A operand of the T contraction: two M = 128 row tiles x (hi, lo) tf32 parts x 128 rows x 16 K; B operand: (hi,
+// lo) x 16 N x 16 K; then the mbarrier of the MMA completion and the TMEM base address.
+constexpr size_t kTcTile = 128 * 64;
+constexpr size_t kTcA = 4 * kTcTile;
+constexpr size_t kTcB = 2 * 16 * 64;
+constexpr size_t kTcBytes = kTcA + kTcB + 16;
+constexpr uint32_t kTcCols = 32;               // TMEM columns: two 128 x 16 FP32 accumulators
+constexpr uint32_t kTcMaxPolls = 1u << 22;     // bound of the MMA-completion wait (one timeout ends all MMAs)
+__host__ __device__ constexpr size_t align128(size_t x) { return (x + 127) & ~size_t(127); }
+
 // largest block of each branch count (J * nb^2 rows, rounded up to warps); two blocks per SM
 // Umklapp candidates of one (q, k1, k2) triple (k3 = q + k1 + k2): bit c set when candidate c is an Umklapp
 // process (Sec. 2.2: q''' = q + s1 q' + s2 q'' + Q with Q != 0), every wavevector taken as its
@@ -389,14 +401,18 @@ __host__ __device__ constexpr int min_blocks_for() { return sizeof(R) == 4 ? FP_
     }                                                                                                  \
   }
 
-template <typename R, int NB, int MAXT>
-__global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rates_kernel(RatesArgs a) {
+// TC: the T contraction of the mixed path on the tensor cores (tcgen05 kind::tf32 in split precision, 3xTF32),
+// for nb = 6 only; the rest of the kernel is unchanged.
+template <typename R, int NB, int MAXT, bool TC = false>
+__global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R>()) rates_kernel(RatesArgs a) {
   constexpr int NB2 = NB * NB, NB3 = NB2 * NB, NA = NB / 3;
   constexpr bool kF64 = sizeof(R) == 8;
+  static_assert(!TC || (!kF64 && NB == 6), "the tensor-core T contraction is built for the mixed path, nb = 6");
   using C = Cx<R>;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long s_item;
   __shared__ unsigned s_umask;  // Umklapp candidates of the current (k1, k2)
+  __shared__ int s_tc_fail;     // a tensor-core completion wait ran out of polls: no further MMAs or waits
   const int J = a.J, G = a.G, nT = a.nT, N = a.N;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int rows = J * NB2;
@@ -469,6 +485,25 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
   const int ebase = (tid >> 5) * kEQCap;
   const int jj_lo = (tid & ~31) / NB2;  // the j0 of this warp's first row; its rows span jj_lo .. jj_lo + S - 1
 
+  // tensor-core state: operand buffers (zeroed once: padding rows and columns stay zero), TMEM accumulators
+  unsigned char* tcbuf = TC ? smem + align128(cv.bytes(sizeof(C))) : smem;
+  uint64_t* s_mbar = reinterpret_cast<uint64_t*>(tcbuf + kTcA + kTcB);
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(tcbuf + kTcA + kTcB + 8);
+  uint32_t tmem_base = 0, tc_phase = 0;
+  if constexpr (TC) {
+    for (int o = tid; o < (int)((kTcA + kTcB) / 16); o += nthr) reinterpret_cast<uint4*>(tcbuf)[o] = make_uint4(0, 0, 0, 0);
+    if ((tid >> 5) == 0) tc::tmem_alloc(s_tmem, kTcCols);
+    if (tid == 0) {
+      s_tc_fail = 0;
+      tc::mbar_init(s_mbar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    tmem_base = *s_tmem;
+  }
   if constexpr (kF64)
     for (int o = tid; o < kExpTab; o += nthr) sExpT[o] = exp(-(double)o * kExpH);
   for (int o = tid; o < NA * NA + 1; o += nthr) sKLs[o] = a.kl_start[o];
@@ -563,6 +598,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
       }
     };
 
+    unsigned icnt = 0;  // accepted terms of this item (the thread's row)
     const int k1_begin = tile * a.t1;
     const int k1_end = min(N, k1_begin + a.t1);
     // unit-vertex (phase-space) mode: q' on a stride, every q'' in one ordering, |W|^2 = 1
@@ -741,13 +777,81 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
               for (int th = 0; th < 3; ++th) cfma(Arow[3 * la + th], tw, ps[th]);
             }
           }
-          C* trow = sT + (size_t)(rjj * NB + rj1) * (NB2 + 1) + rc * NB;
+          if constexpr (TC) {
+            // A operand row tid (real part in K 0..5, imaginary in K 6..11), split into tf32 hi + lo
+            unsigned char* Ah = tcbuf + (size_t)(tid >> 7) * 2 * kTcTile;
+            const int r = tid & 127;
 #pragma unroll
-          for (int j3 = 0; j3 < NB; ++j3) {
-            C s = cmk<R>(0, 0);
+            for (int k = 0; k < 2 * NB; ++k) {
+              const float x = k < NB ? (float)Arow[k].re : (float)Arow[k - NB].im;
+              const float hi = tc::to_tf32(x);
+              const uint32_t off = tc::kmajor_offset(r, k);
+              *reinterpret_cast<float*>(Ah + off) = hi;
+              *reinterpret_cast<float*>(Ah + kTcTile + off) = tc::to_tf32(x - hi);
+            }
+          } else {
+            C* trow = sT + (size_t)(rjj * NB + rj1) * (NB2 + 1) + rc * NB;
 #pragma unroll
-            for (int d = 0; d < NB; ++d) cfma_conj(s, Arow[d], sE3[j3 * NB + d]);
-            trow[j3] = s;
+            for (int j3 = 0; j3 < NB; ++j3) {
+              C s = cmk<R>(0, 0);
+#pragma unroll
+              for (int d = 0; d < NB; ++d) cfma_conj(s, Arow[d], sE3[j3 * NB + d]);
+              trow[j3] = s;
+            }
+          }
+        }
+        if constexpr (TC) {
+          if (!unit) {
+            // B operand: T = A conj(E3)^T as a real product; column n = 2 j3 (+1) gives Re (Im) of T[.][j3]
+            unsigned char* Bh = tcbuf + kTcA;
+            for (int o = tid; o < 2 * NB * 2 * NB; o += nthr) {
+              const int n = o / (2 * NB), k = o % (2 * NB);
+              const int j3 = n >> 1, d = k % NB;
+              const C ev = sE3[j3 * NB + d];
+              const bool im_col = n & 1, im_row = k >= NB;
+              const float x = !im_col ? (!im_row ? (float)ev.re : (float)ev.im) : (!im_row ? -(float)ev.im : (float)ev.re);
+              const float hi = tc::to_tf32(x);
+              const uint32_t off = tc::kmajor_offset(n, k);
+              *reinterpret_cast<float*>(Bh + off) = hi;
+              *reinterpret_cast<float*>(Bh + 1024 + off) = tc::to_tf32(x - hi);
+            }
+            tc::fence_async_smem();
+            __syncthreads();
+            const bool live = s_tc_fail == 0;  // uniform: read after the barrier above
+            if (tid == 0 && live) {
+              tc::fence_after_sync();
+              constexpr uint32_t idesc = tc::idesc_tf32(128, 16);
+              const uint32_t b0 = tc::smem_u32(Bh);
+#pragma unroll
+              for (int t = 0; t < 2; ++t) {
+                const uint32_t a0 = tc::smem_u32(tcbuf + (size_t)t * 2 * kTcTile);
+                const uint32_t d = tmem_base + (uint32_t)(t * 16);
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks) {  // K = 16 in two steps of 8 (two core matrices, 256 bytes)
+                  const uint32_t ko = (uint32_t)ks * 2u * tc::kLbo;
+                  tc::mma_tf32(d, tc::make_desc(a0 + ko), tc::make_desc(b0 + ko), idesc, ks);
+                  tc::mma_tf32(d, tc::make_desc(a0 + ko), tc::make_desc(b0 + 1024 + ko), idesc, 1);
+                  tc::mma_tf32(d, tc::make_desc(a0 + (uint32_t)kTcTile + ko), tc::make_desc(b0 + ko), idesc, 1);
+                }
+              }
+              tc::mma_commit(s_mbar);
+            }
+            const bool done = live && tc::mbar_wait(s_mbar, tc_phase, kTcMaxPolls);
+            tc_phase ^= 1u;
+            if (live && !done) {
+              s_tc_fail = 1;
+              if (lane == 0) atomicAdd(a.counts + 5, 1ULL);
+            }
+            tc::fence_after_sync();
+            const int warp = tid >> 5;
+            float v[16];
+            tc::tmem_ld16(tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * 16), v);
+            if (has_row) {
+              C* trow = sT + (size_t)(rjj * NB + rj1) * (NB2 + 1) + rc * NB;
+#pragma unroll
+              for (int j3 = 0; j3 < NB; ++j3) trow[j3] = cmk<R>(v[2 * j3], v[2 * j3 + 1]);
+            }
+            tc::fence_before_sync();
           }
         }
         __syncthreads();
@@ -854,6 +958,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
               cnt1 += row_mult * __popc(accm & 0x12u);
               cnt2 += row_mult * __popc(accm & 0x24u);
               nte += __popc(accm);
+              icnt += __popc(accm);
             }
             // entries with an accepted candidate, one per lane at most, in lane order
             const unsigned bal = __ballot_sync(0xffffffffu, accm != 0);
@@ -916,6 +1021,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
                 cnt1 += row_mult * __popc(accm & 0x12u);
                 cnt2 += row_mult * __popc(accm & 0x24u);
                 nte += __popc(accm);
+                icnt += __popc(accm);
                 C Wv = cmk<R>(unit ? 1 : 0, 0);
                 if (!unit) {
                   ++nwf;
@@ -1011,6 +1117,18 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
       a.partial[(size_t)item * J * nT + o] = sum;
     }
     __syncthreads();
+    if (a.item_counts) {
+      // accepted terms per j0 of the item: the rows jj * nb^2 .. (jj + 1) * nb^2 - 1, in row order
+      unsigned long long* sCnt = reinterpret_cast<unsigned long long*>(sRed);  // reuses the reduction buffer
+      sCnt[tid] = icnt;
+      __syncthreads();
+      for (int jj = tid; jj < J; jj += nthr) {
+        unsigned long long sum = 0;
+        for (int r = jj * NB2; r < (jj + 1) * NB2; ++r) sum += sCnt[r];
+        a.item_counts[(size_t)item * J + jj] = sum;
+      }
+      __syncthreads();
+    }
   }
   // accepted counts and vertex entries formed
   for (int off = 16; off > 0; off >>= 1) {
@@ -1026,6 +1144,14 @@ __global__ void __launch_bounds__(max_threads_for(NB), min_blocks_for<R>()) rate
     if (cnt2) atomicAdd(a.counts + 2, cnt2);
     if (nwf) atomicAdd(a.counts + 3, nwf);
     if (nte) atomicAdd(a.counts + 4, nte);
+  }
+  if constexpr (TC) {
+    tc::fence_before_sync();
+    __syncthreads();
+    if ((tid >> 5) == 0) {
+      tc::fence_after_sync();
+      tc::tmem_dealloc(tmem_base, kTcCols);
+    }
   }
 }
 

@@ -563,21 +563,44 @@ extern "C" int fp_surrogate_fit(fp_ctx* c, int nT, const double* T, double sb, c
   const int nb = c->nb, nm = c->N * nb, F = nb + 13;
   const size_t rows_all = (size_t)nm * nT;
 
-  // modes with positive frequency, shuffled with the seeded generator
+  // modes with positive frequency
   std::vector<double> om(nm);
   SG_CUDA(c, cudaMemcpyAsync(om.data(), c->d_omega, nm * sizeof(double), cudaMemcpyDeviceToHost, s));
   SG_CUDA(c, cudaStreamSynchronize(s));
   std::vector<int> pos;
   for (int m = 0; m < nm; ++m)
     if (om[m] > 0.0) pos.push_back(m);
+  // training and held-out modes are drawn as whole pairs {q, -q} with all their branches: the rate path evaluates
+  // a pair at once (time reversal), so the exact share of the cost is the share of pairs drawn
+  std::vector<std::vector<int>> units;
+  {
+    std::vector<char> seen(c->N, 0);
+    for (int q = 0; q < c->N; ++q) {
+      if (seen[q]) continue;
+      const int g0 = q / (c->grid[1] * c->grid[2]), g1 = (q / c->grid[2]) % c->grid[1], g2 = q % c->grid[2];
+      const int p = (((c->grid[0] - g0) % c->grid[0]) * c->grid[1] + (c->grid[1] - g1) % c->grid[1]) * c->grid[2] +
+                    (c->grid[2] - g2) % c->grid[2];
+      seen[q] = seen[p] = 1;
+      std::vector<int> u;
+      const int members[2] = {q, p};
+      for (int k = 0; k < (p == q ? 1 : 2); ++k)
+        for (int j = 0; j < nb; ++j)
+          if (om[(size_t)members[k] * nb + j] > 0.0) u.push_back(members[k] * nb + j);
+      if (!u.empty()) units.push_back(u);
+    }
+  }
   SplitMix64 rng{so.seed};
-  for (size_t i = pos.size(); i > 1; --i) std::swap(pos[i - 1], pos[rng.next() % i]);
-  const int n_train = std::max(1, (int)std::ceil(so.train_frac * pos.size()));
-  const int n_hold = std::max(1, (int)std::ceil(so.holdout_frac * pos.size()));
-  if (n_train + n_hold > (int)pos.size()) return sfail(c, FP_EINVAL, "fp_surrogate_fit: too few modes");
+  for (size_t i = units.size(); i > 1; --i) std::swap(units[i - 1], units[rng.next() % i]);
+  const int u_train = std::max(1, (int)std::ceil(so.train_frac * units.size()));
+  const int u_hold = std::max(1, (int)std::ceil(so.holdout_frac * units.size()));
+  if (u_train + u_hold > (int)units.size()) return sfail(c, FP_EINVAL, "fp_surrogate_fit: too few modes");
   std::vector<unsigned char> role(nm, 0);  // 1 train, 2 holdout, 3 fallback
-  for (int i = 0; i < n_train; ++i) role[pos[i]] = 1;
-  for (int i = n_train; i < n_train + n_hold; ++i) role[pos[i]] = 2;
+  int n_train = 0, n_hold = 0;
+  for (int i = 0; i < u_train + u_hold; ++i)
+    for (int m : units[i]) {
+      role[m] = i < u_train ? 1 : 2;
+      (i < u_train ? n_train : n_hold) += 1;
+    }
 
   // exact rates of the training and held-out modes (one batched evaluation for all temperatures)
   double t0 = now_ms();

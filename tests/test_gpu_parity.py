@@ -16,9 +16,10 @@ from conftest import oracle_modes
 pytestmark = pytest.mark.gpu
 
 RTOL_FP64 = 1e-10
-# mixed path: FP32 vertex assembly/contraction and Gaussian, exact decisions, FP64 sums; the bound is
-# the measured worst case with a 10x margin (see the mixed-precision test below)
-RTOL_MIXED = 2e-4
+# mixed path: FP32 vertex assembly/contraction and Gaussian, exact decisions, FP64 sums.  Measured worst cases
+# against the FP64 oracle: 2.7e-7 on the small grids here, 9.9e-8 (BAs 12^3), 1.8e-7 (LiCoO2 10x10x6, against the
+# FP64 path), 2.2e-7 (diamond 16^3, 8 temperatures); the bound is about 10x the worst
+RTOL_MIXED = 3e-6
 
 
 @pytest.fixture(scope="module")
@@ -328,3 +329,37 @@ def test_time_reversal_evaluates_half_the_grid(lib, maker):
         assert st_f["vertex_entries"] == st_e["vertex_entries"]
     for q in range(N):
         assert np.array_equal(fold[:, q], fold[:, _neg_index(cr.grid, q)])
+
+
+@pytest.mark.parametrize("maker,tiles", [(lambda: synth.diamond_si((3, 3, 2)), {}),
+                                         (lambda: synth.zincblende_bas((3, 3, 3)), {}),
+                                         (lambda: synth.diamond_si((4, 4, 3)), dict(block_j0=3, k1_tile=2, threads=128)),
+                                         (lambda: synth.diamond_si((3, 2, 2)), dict(block_j0=1, k1_tile=1, threads=64))],
+                         ids=["diamond-3x3x2", "bas-3x3x3", "diamond-4x4x3-J3", "diamond-3x2x2-J1"])
+def test_tensor_core_contraction(lib, maker, tiles):
+    """The mixed path with the per-q'' contraction T = A conj(E3) on the tensor cores (tcgen05 kind::tf32, 3xTF32,
+    FP32 accumulation in tensor memory): within the mixed bound of the oracle, exact accepted counts, one and
+    three temperatures, and row tiles that fill two, one or a fraction of an M = 128 tile."""
+    cr = maker()
+    w, e, v = oracle_modes(cr)
+    for temps in ([300.0], [300.0, 600.0, 900.0]):
+        ref, acc = oracle.rates4(cr, w, e, v, temps=temps)
+        out, st = run_gpu(lib, cr, w, e, v, temps=temps, precision=FP_PREC_MIXED, tensor_cores=1, **tiles)
+        simt, _ = run_gpu(lib, cr, w, e, v, temps=temps, precision=FP_PREC_MIXED, **tiles)
+        err = compare(out.reshape(len(temps), -1), ref, RTOL_MIXED)
+        assert np.array_equal(np.array(st["accepted"]), acc)
+        print(f"{cr.name} {cr.grid} nT={len(temps)}: tensor-core mixed err {err:.2e}, "
+              f"CUDA-core mixed err {compare(simt.reshape(len(temps), -1), ref, RTOL_MIXED):.2e}")
+
+
+def test_tensor_cores_reject_other_paths(lib):
+    cr = synth.simple_cubic((2, 2, 2))
+    w, e, v = oracle_modes(cr)
+    with pytest.raises(lib.FourPhononError):
+        run_gpu(lib, cr, w, e, v, precision=FP_PREC_MIXED, tensor_cores=1)   # nb = 3
+    cr = synth.diamond_si((2, 2, 2))
+    w, e, v = oracle_modes(cr)
+    with pytest.raises(lib.FourPhononError):
+        run_gpu(lib, cr, w, e, v, precision=FP_PREC_FP64, tensor_cores=1)
+    with pytest.raises(lib.FourPhononError):
+        run_gpu(lib, cr, w, e, v, precision=FP_PREC_MIXED, tensor_cores=2)

@@ -255,3 +255,39 @@ def test_rates_are_intensive():
         rates.append(r)
     assert rates[0].min() > 0
     np.testing.assert_allclose(rates[1], rates[0], rtol=1e-12, atol=0.0)
+
+
+def test_phase_space_p4_single_q_closed_form():
+    """The unweighted phase space (BTE.P4 of Appendix A, the rate's sum with the vertex, Bose and frequency factors
+    set to 1): with zero velocities and integer frequencies only exactly conserving terms enter, each with delta := 1,
+    so P4 of each mode is 1/2 n++ + 1/2 n+- + 1/6 n-- with n_p its accepted counts (pinned by enumeration)."""
+    cr = synth.diamond_si((1, 1, 1))
+    omega = np.array([[3.0, 1.0, 1.0, 2.0, 4.0, 6.0]])
+    evec = np.eye(6, dtype=complex)[None]
+    vel = np.zeros((1, 6, 3))
+    for lam in range(6):
+        p4, acc = oracle.rates4(cr, omega, evec, vel, temps=[T], sel=[lam], unit_vertex=2)
+        assert p4[0, 0] == pytest.approx(0.5 * acc[0] + 0.5 * acc[1] + acc[2] / 6.0, rel=1e-13, abs=0)
+        if lam == 0:
+            assert acc.min() > 0
+
+
+def test_phase_space_p4_is_the_swept_gaussian():
+    """With the unit weights the swept family of test_gaussian... contributes 4 * 1/2 * delta(s): the P4 sum over the
+    sweep is 2 erf(window) times the step, whatever sigma is."""
+    lattice, grid, va, vb, sb, dq_mode = GEOMETRIES[0]
+    cr = grid_crystal(lattice, grid)
+    N = cr.nq
+    sig = hand_sigma(lattice, grid, [va[k] - vb[k] for k in range(3)], sb, dq_mode)
+    evec = np.tile(np.eye(3, dtype=complex)[None], (N, 1, 1))
+    vel = np.zeros((N, 3, 3))
+    vel[0] = [va, va, vb]
+    n = 600
+    h = 2.2 * WINDOW * sig / n
+    total = 0.0
+    for s in -1.1 * WINDOW * sig + h * (np.arange(n) + 0.5):
+        omega = np.tile(np.array([[50.0, 60.0, 70.0]]), (N, 1))
+        omega[0] = [1.0, 1.0, 3.0 + s]
+        r, _ = oracle.rates4(cr, omega, evec, vel, temps=[T], scalebroad=sb, sel=[0], unit_vertex=2, processes=(0,))
+        total += r[0, 0] * h
+    assert total == pytest.approx(2.0 * math.erf(WINDOW), abs=5e-4)
