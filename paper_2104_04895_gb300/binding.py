@@ -21,6 +21,7 @@ FP_EUNSTABLE = -4
 FP_ESTATE = -6
 FP_PREC_FP64 = 0
 FP_PREC_MIXED = 1
+FP_PREC_DOUBLE_FLOAT = 2
 
 
 class fp_fc2(ctypes.Structure):

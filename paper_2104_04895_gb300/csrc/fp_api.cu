@@ -414,7 +414,7 @@ static int validate_opts(fp_ctx* c, int nT, const double* T, double sb, const fp
     if (!(T[i] > 0.0) || !std::isfinite(T[i])) return fail(c, FP_EINVAL, "fp_rates4: temperatures must be > 0");
   if (!(sb > 0.0) || !std::isfinite(sb)) return fail(c, FP_EINVAL, "fp_rates4: scalebroad must be > 0");
   if (!(o->window > 0.0) || !(o->sigma_min > 0.0)) return fail(c, FP_EINVAL, "fp_rates4: window, sigma_min > 0");
-  if (o->precision != FP_PREC_FP64 && o->precision != FP_PREC_MIXED)
+  if (o->precision != FP_PREC_FP64 && o->precision != FP_PREC_MIXED && o->precision != FP_PREC_DOUBLE_FLOAT)
     return fail(c, FP_EINVAL, "fp_rates4: unknown precision");
   if (o->dq_mode != 0 && o->dq_mode != 1) return fail(c, FP_EINVAL, "fp_rates4: dq_mode must be 0 or 1");
   if (o->process_mask < 0 || o->process_mask > 7)

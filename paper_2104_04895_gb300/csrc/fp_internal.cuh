@@ -170,8 +170,8 @@ struct fp_ctx {
   int* d_star = nullptr;  // star representatives (fp_rates4_irreducible)
   size_t star_cap = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  // tiles chosen by fp_autotune, per (precision, one or several temperatures): J, k1 tile, threads
-  int tuned[2][2][3] = {{{0, 0, 0}, {0, 0, 0}}, {{0, 0, 0}, {0, 0, 0}}};
+  // tiles chosen by fp_autotune, per (precision FP_PREC_*, one or several temperatures): J, k1 tile, threads
+  int tuned[3][2][3] = {};
   // the captured rate step and the launch parameters it was captured with
   cudaGraphExec_t graph_exec = nullptr;
   std::vector<unsigned char> graph_key;

@@ -80,7 +80,7 @@ extern "C" int fp_rates4_noalloc(fp_ctx* c, int nT, const double* T, double sb, 
   if (!(sb > 0.0) || !std::isfinite(sb)) return nfail(c, FP_EINVAL, "fp_rates4_noalloc: scalebroad must be > 0");
   if (!(o.window > 0.0) || !(o.sigma_min > 0.0))
     return nfail(c, FP_EINVAL, "fp_rates4_noalloc: window, sigma_min must be > 0");
-  if (o.precision != FP_PREC_FP64 && o.precision != FP_PREC_MIXED)
+  if (o.precision != FP_PREC_FP64 && o.precision != FP_PREC_MIXED && o.precision != FP_PREC_DOUBLE_FLOAT)
     return nfail(c, FP_EINVAL, "fp_rates4_noalloc: unknown precision");
   if (o.dq_mode != 0 && o.dq_mode != 1) return nfail(c, FP_EINVAL, "fp_rates4_noalloc: dq_mode must be 0 or 1");
   if (o.process_mask < 0 || o.process_mask > 7)

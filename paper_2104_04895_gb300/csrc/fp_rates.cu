@@ -8,6 +8,7 @@ namespace fp {
 const void* rates_kernel_f64(int nb, int maxt);
 const void* rates_kernel_f32(int nb, int maxt);
 const void* rates_kernel_f32_tc(int nb, int maxt);
+const void* rates_kernel_df(int nb, int maxt);
 
 namespace {
 
@@ -95,12 +96,14 @@ __global__ void fill_kernel(double* p, long long n, double v) {
 const void* rates_kernel_ptr(int precision, int nb, int nT, bool tc) {
   const int maxt = nT == 1 ? 1 : kMaxT;
   if (tc) return precision == FP_PREC_MIXED ? rates_kernel_f32_tc(nb, maxt) : nullptr;
+  if (precision == FP_PREC_DOUBLE_FLOAT) return rates_kernel_df(nb, maxt);
   return precision == FP_PREC_FP64 ? rates_kernel_f64(nb, maxt) : rates_kernel_f32(nb, maxt);
 }
 
 size_t smem_bytes(int precision, int nb, int J, int G, int nquart, int nT, int threads, bool tc) {
-  Carve c = make_carve(nb, J, G, nquart, nT, threads, precision != FP_PREC_FP64);
-  const size_t b = c.bytes(precision == FP_PREC_FP64 ? sizeof(Cx<double>) : sizeof(Cx<float>));
+  const bool f32 = precision == FP_PREC_MIXED;  // the double-float path has the FP64 path's shared memory
+  Carve c = make_carve(nb, J, G, nquart, nT, threads, f32);
+  const size_t b = c.bytes(f32 ? sizeof(Cx<float>) : sizeof(Cx<double>));
   return tc ? align128(b) + kTcBytes : b;
 }
 
@@ -181,7 +184,7 @@ int plan_rates(fp_ctx* c, const fp_rates_opts& o, int nT, Selection& sel, size_t
   int J = o.block_j0;
   int t1_tuned = 0, th_tuned = 0;
   if (J <= 0 && o.k1_tile <= 0 && o.threads <= 0) {
-    const int* tt = c->tuned[o.precision == FP_PREC_FP64 ? 0 : 1][nT == 1 ? 0 : 1];
+    const int* tt = c->tuned[o.precision][nT == 1 ? 0 : 1];
     if (tt[0] > 0) {
       J = tt[0];
       t1_tuned = tt[1];
@@ -395,7 +398,7 @@ int run_rates(fp_ctx* c, const fp_rates_opts& o, const Selection& sel, const Pla
   a.mode_counts = x.d_mode_counts;
   a.count_scale = unit_stride > 0 ? (double)unit_stride : 1.0;
 
-  const int want_f32 = o.precision != FP_PREC_FP64;
+  const int want_f32 = o.precision == FP_PREC_MIXED;
   const double conv = kConv;
   // unit-vertex mode: no physical prefactor; scale the strided ordered-pair sum to the full grid
   const double pref = unit_stride > 0

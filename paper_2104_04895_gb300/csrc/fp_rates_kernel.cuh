@@ -106,6 +106,54 @@ __device__ __forceinline__ float ld_fc<float>(const RatesArgs& a, size_t i) {
   return a.qfcf[i];
 }
 
+// Double-float arithmetic for the FP64-accurate vertex contraction of FP_PREC_DOUBLE_FLOAT: a real is a pair of
+// floats (h, l) with value h + l; a complex is a float4 (re.h, re.l, im.h, im.l).  A product keeps the high parts'
+// product exactly (fma residual) and the cross terms in FP32; a sum adds the high parts by Knuth's two-sum and the
+// low parts in FP32, so each operation keeps about 48 bits (Dekker 1971; the pair is renormalised when stored).
+__device__ __forceinline__ float4 cdf_from(double re, double im) {
+  const float rh = __double2float_rn(re), ih = __double2float_rn(im);
+  return make_float4(rh, __double2float_rn(re - (double)rh), ih, __double2float_rn(im - (double)ih));
+}
+// (h, l) += (ah + al) (bh + bl), dropping al bl
+__device__ __forceinline__ void df_mac(float& h, float& l, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  const float e = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, __fmaf_rn(ah, bh, -p)));
+  const float s = __fadd_rn(h, p);
+  const float bb = __fsub_rn(s, h);
+  const float t = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  l = __fadd_rn(l, __fadd_rn(t, e));
+  h = s;
+}
+// acc += a * b
+__device__ __forceinline__ void cdf_mac(float4& acc, float4 a, float4 b) {
+  df_mac(acc.x, acc.y, a.x, a.y, b.x, b.y);
+  df_mac(acc.x, acc.y, -a.z, -a.w, b.z, b.w);
+  df_mac(acc.z, acc.w, a.x, a.y, b.z, b.w);
+  df_mac(acc.z, acc.w, a.z, a.w, b.x, b.y);
+}
+// acc += a * conj(b)
+__device__ __forceinline__ void cdf_mac_conj(float4& acc, float4 a, float4 b) {
+  df_mac(acc.x, acc.y, a.x, a.y, b.x, b.y);
+  df_mac(acc.x, acc.y, a.z, a.w, b.z, b.w);
+  df_mac(acc.z, acc.w, a.z, a.w, b.x, b.y);
+  df_mac(acc.z, acc.w, -a.x, -a.y, b.z, b.w);
+}
+// (h, l) with |l| <= ulp(h) / 2 (fast two-sum; |h| >= |l| after the accumulation above)
+__device__ __forceinline__ float4 cdf_norm(float4 a) {
+  const float rs = __fadd_rn(a.x, a.y), is = __fadd_rn(a.z, a.w);
+  return make_float4(rs, __fsub_rn(a.y, __fsub_rn(rs, a.x)), is, __fsub_rn(a.w, __fsub_rn(is, a.z)));
+}
+// |w|^2 in double from a double-float complex: squares with exact high products, two-sum of the two squares
+__device__ __forceinline__ double cdf_abs2(float4 w) {
+  const float ph = __fmul_rn(w.x, w.x), qh = __fmul_rn(w.z, w.z);
+  const float pe = __fmaf_rn(2.0f * w.x, w.y, __fmaf_rn(w.x, w.x, -ph));
+  const float qe = __fmaf_rn(2.0f * w.z, w.w, __fmaf_rn(w.z, w.z, -qh));
+  const float s = __fadd_rn(ph, qh);
+  const float bb = __fsub_rn(s, ph);
+  const float t = __fadd_rn(__fsub_rn(ph, __fsub_rn(s, bb)), __fsub_rn(qh, bb));
+  return (double)s + (double)__fadd_rn(t, __fadd_rn(pe, qe));
+}
+
 __device__ __forceinline__ int wrapi(int x, int n) {
   int r = x % n;
   return r < 0 ? r + n : r;
@@ -403,11 +451,15 @@ __host__ __device__ constexpr int min_blocks_for() { return sizeof(R) == 4 ? FP_
 
 // TC: the T contraction of the mixed path on the tensor cores (tcgen05 kind::tf32 in split precision, 3xTF32),
 // for nb = 6 only; the rest of the kernel is unchanged.
-template <typename R, int NB, int MAXT, bool TC = false>
+// DF: the FP64 path with its vertex contraction (A, T, W) in double-float on the FP32 pipes (Psi, twiddles and
+// eigenvectors stored as float pairs in the same shared-memory slots); everything else as in the FP64 path.
+template <typename R, int NB, int MAXT, bool TC = false, bool DF = false>
 __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R>()) rates_kernel(RatesArgs a) {
-  constexpr int NB2 = NB * NB, NB3 = NB2 * NB, NA = NB / 3;
+  constexpr int NB2 = NB * NB, NA = NB / 3;
   constexpr bool kF64 = sizeof(R) == 8;
+  constexpr bool kDF = DF;
   static_assert(!TC || (!kF64 && NB == 6), "the tensor-core T contraction is built for the mixed path, nb = 6");
+  static_assert(!DF || kF64, "the double-float contraction belongs to the FP64 path");
   using C = Cx<R>;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long s_item;
@@ -674,8 +726,14 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
             cfma(sum[u], tq, s);
           }
         }
+        if constexpr (kDF) {
 #pragma unroll
-        for (int u = 0; u < kGtb; ++u) sPsi[(size_t)t9 * 9 + gb * kGtb + u] = sum[u];
+          for (int u = 0; u < kGtb; ++u)
+            reinterpret_cast<float4*>(sPsi)[(size_t)t9 * 9 + gb * kGtb + u] = cdf_from(sum[u].re, sum[u].im);
+        } else {
+#pragma unroll
+          for (int u = 0; u < kGtb; ++u) sPsi[(size_t)t9 * 9 + gb * kGtb + u] = sum[u];
+        }
       }
       __syncthreads();
 
@@ -701,8 +759,14 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
         const int k3 = (g3[0] * a.grid[1] + g3[1]) * a.grid[2] + g3[2];
         if (a.nu_select != 0 && tid == 0) s_umask = umklapp_bits(a, g, g1, g2, g3);  // read after the barrier
         for (int o = tid; o < NB2; o += nthr) {
-          sE2[o] = ld_e<R>(a, (size_t)k2 * NB2 + o);
-          sE3[o] = ld_e<R>(a, (size_t)k3 * NB2 + o);
+          if constexpr (kDF) {
+            const double2 e2v = a.evec[(size_t)k2 * NB2 + o], e3v = a.evec[(size_t)k3 * NB2 + o];
+            reinterpret_cast<float4*>(sE2)[o] = cdf_from(e2v.x, e2v.y);
+            reinterpret_cast<float4*>(sE3)[o] = cdf_from(e3v.x, e3v.y);
+          } else {
+            sE2[o] = ld_e<R>(a, (size_t)k2 * NB2 + o);
+            sE3[o] = ld_e<R>(a, (size_t)k3 * NB2 + o);
+          }
         }
         for (int o = tid; o < NB; o += nthr) {
           sOm2[o] = a.omega[k2 * NB + o];
@@ -741,7 +805,12 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
           int e = 0;  // each term is below L, so e < 3 L
           for (int d = 0; d < 3; ++d) e += a.Lfac[d] * wrapi(g2[d] * gm[2 + d], a.grid[d]);
           while (e >= a.L) e -= a.L;
-          sTw2[gi] = ld_tw<R>(a, e);
+          if constexpr (kDF) {
+            const double2 t = a.tw[e];
+            reinterpret_cast<float4*>(sTw2)[gi] = cdf_from(t.x, t.y);
+          } else {
+            sTw2[gi] = ld_tw<R>(a, e);
+          }
         }
         __syncthreads();
         // ---- phase 2: sigma tables; A row and T row
@@ -759,7 +828,37 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
             sigma_f_from_exact(sSig + 2 * o, sSigPM + o, sSigI + o);
           }
         }
-        if (has_row && !unit) {
+        if constexpr (kDF) {
+          if (has_row && !unit) {
+            // A row and T row in double-float
+            float4 Ad[NB];
+#pragma unroll
+            for (int d = 0; d < NB; ++d) Ad[d] = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int ka = rc / 3, ga = rc % 3;
+            const float4* psi_row = reinterpret_cast<const float4*>(sPsi) + (size_t)(rjj * NB + rj1) * G * 9 + ga * 3;
+            const float4* twd = reinterpret_cast<const float4*>(sTw2);
+#pragma unroll
+            for (int la = 0; la < NA; ++la) {
+              const int kl = ka * NA + la;
+              for (int gi = sKLs[kl]; gi < sKLs[kl + 1]; ++gi) {
+                const int grp = sKLg[gi];
+                const float4 tw = twd[grp];
+                const float4* ps = psi_row + grp * 9;
+#pragma unroll
+                for (int th = 0; th < 3; ++th) cdf_mac(Ad[3 * la + th], tw, ps[th]);
+              }
+            }
+            const float4* e3d = reinterpret_cast<const float4*>(sE3);
+            float4* trow = reinterpret_cast<float4*>(sT + (size_t)(rjj * NB + rj1) * (NB2 + 1) + rc * NB);
+#pragma unroll
+            for (int j3 = 0; j3 < NB; ++j3) {
+              float4 sd = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+              for (int d = 0; d < NB; ++d) cdf_mac_conj(sd, Ad[d], e3d[j3 * NB + d]);
+              trow[j3] = cdf_norm(sd);
+            }
+          }
+        } else if (has_row && !unit) {
           // A row (jj, j1 = rj1, c = rc): d = (l, theta)
           C Arow[NB];
 #pragma unroll
@@ -903,12 +1002,21 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
             if (ent && !unit) {
               ++nwf;
               const int ej3 = (ent >> 6) & 15, ey = (ent >> 10) & 15, ex = (ent >> 14) & 15, ejq = ent >> 18;
-              const C* tbe = sT + (size_t)(ejq * NB + ex) * (NB2 + 1) + ej3;
-              const C* e2 = sE2 + ey * NB;
-              C Wv = cmk<R>(0, 0);
+              if constexpr (kDF) {
+                const float4* tbe = reinterpret_cast<const float4*>(sT + (size_t)(ejq * NB + ex) * (NB2 + 1) + ej3);
+                const float4* e2 = reinterpret_cast<const float4*>(sE2 + ey * NB);
+                float4 Wd = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-              for (int c = 0; c < NB; ++c) cfma(Wv, e2[c], tbe[c * NB]);
-              W2 = Wv.re * Wv.re + Wv.im * Wv.im;
+                for (int c = 0; c < NB; ++c) cdf_mac(Wd, e2[c], tbe[c * NB]);
+                W2 = cdf_abs2(Wd);
+              } else {
+                const C* tbe = sT + (size_t)(ejq * NB + ex) * (NB2 + 1) + ej3;
+                const C* e2 = sE2 + ey * NB;
+                C Wv = cmk<R>(0, 0);
+#pragma unroll
+                for (int c = 0; c < NB; ++c) cfma(Wv, e2[c], tbe[c * NB]);
+                W2 = Wv.re * Wv.re + Wv.im * Wv.im;
+              }
             }
             unsigned m = ent & 63u;
             const int nmy = __popc(m);

@@ -18,6 +18,8 @@ extern "C" int fp_autotune(fp_ctx* c, int nT, const double* T, double scalebroad
   if (!c || !opts) return FP_EINVAL;
   if (!c->have_modes) return tfail(c, FP_ESTATE, "fp_autotune: call fp_modes or fp_set_modes first");
   if (nT < 1 || nT > fp::kMaxT || !T) return tfail(c, FP_EINVAL, "fp_autotune: nT must be in [1, 8]");
+  if (opts->precision < FP_PREC_FP64 || opts->precision > FP_PREC_DOUBLE_FLOAT)
+    return tfail(c, FP_EINVAL, "fp_autotune: unknown precision");
   const int N = c->N, nb = c->nb;
   const int maxth = nb == 3 ? 128 : nb == 6 ? 224 : 160;
   // q sample: about 64 x 512^2 (q, q', q'') triples per trial (a few percent of a 512-point grid), and at
@@ -65,7 +67,7 @@ extern "C" int fp_autotune(fp_ctx* c, int nT, const double* T, double scalebroad
   }
   cudaFree(d_out);
   if (bj == 0) return tfail(c, FP_EINVAL, "fp_autotune: no tile could run");
-  int* tt = c->tuned[opts->precision == FP_PREC_FP64 ? 0 : 1][nT == 1 ? 0 : 1];
+  int* tt = c->tuned[opts->precision][nT == 1 ? 0 : 1];
   tt[0] = bj;
   tt[1] = bt;
   tt[2] = bth;

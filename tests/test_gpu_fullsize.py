@@ -21,7 +21,7 @@ import pytest
 
 import oracle
 from paper_2104_04895_gb300 import synth
-from paper_2104_04895_gb300.binding import FP_PREC_FP64, FP_PREC_MIXED
+from paper_2104_04895_gb300.binding import FP_PREC_DOUBLE_FLOAT, FP_PREC_FP64, FP_PREC_MIXED
 
 from conftest import oracle_modes
 
@@ -96,13 +96,16 @@ def test_bas_12_full_size(lib):
         ctx.set_modes(w, e, v)
         out, st = ctx.rates4(cr.temps, cr.scalebroad, mode_mask=mask)
         outm, stm = ctx.rates4(cr.temps, cr.scalebroad, mode_mask=mask, precision=FP_PREC_MIXED)
+        outd, std_ = ctx.rates4(cr.temps, cr.scalebroad, mode_mask=mask, precision=FP_PREC_DOUBLE_FLOAT)
         counts = gpu_single_mode_counts(ctx, cr, cr.temps, count_only)
     got = out.reshape(1, -1)[:, full_vertex]
     gotm = outm.reshape(1, -1)[:, full_vertex]
     err = rel_err(got, ref)
     errm = rel_err(gotm, ref)
-    print(f"BAs 12^3 full size: FP64 {err:.2e}, mixed {errm:.2e} on modes {full_vertex}")
-    assert err <= RTOL_FP64
+    errd = rel_err(outd.reshape(1, -1)[:, full_vertex], ref)
+    print(f"BAs 12^3 full size: FP64 {err:.2e}, double-float {errd:.2e}, mixed {errm:.2e} on modes {full_vertex}")
+    assert err <= RTOL_FP64 and errd <= RTOL_FP64
+    assert np.array_equal(np.array(std_["accepted"]), acc)
     assert errm <= RTOL_MIXED
     assert np.array_equal(np.array(st["accepted"]), acc) and np.array_equal(np.array(stm["accepted"]), acc)
     assert np.all(out.reshape(-1)[mask == 0] == 0.0)

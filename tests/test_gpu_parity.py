@@ -363,3 +363,36 @@ def test_tensor_cores_reject_other_paths(lib):
         run_gpu(lib, cr, w, e, v, precision=FP_PREC_FP64, tensor_cores=1)
     with pytest.raises(lib.FourPhononError):
         run_gpu(lib, cr, w, e, v, precision=FP_PREC_MIXED, tensor_cores=2)
+
+
+@pytest.mark.parametrize("name,maker", CASES, ids=[c[0] for c in CASES])
+def test_double_float_parity_small(lib, name, maker):
+    """FP_PREC_DOUBLE_FLOAT (the FP64 path with its vertex contraction in pairs of floats on the FP32 pipes) holds
+    the FP64 bar: 1e-10 of the oracle and exact accepted counts."""
+    from paper_2104_04895_gb300.binding import FP_PREC_DOUBLE_FLOAT
+    cr = maker()
+    w, e, v = oracle_modes(cr)
+    ref, acc = oracle.rates4(cr, w, e, v)
+    out, st = run_gpu(lib, cr, w, e, v, precision=FP_PREC_DOUBLE_FLOAT)
+    err = compare(out.reshape(len(cr.temps), -1), ref, RTOL_FP64)
+    assert np.array_equal(np.array(st["accepted"]), acc)
+    print(f"{name}: double-float max rel err {err:.2e}")
+
+
+@pytest.mark.parametrize("tiles", [dict(block_j0=1, k1_tile=3, threads=64), dict(block_j0=3, k1_tile=7, threads=96)])
+def test_double_float_tilings_temperatures_and_dq_mode(lib, tiles):
+    from paper_2104_04895_gb300.binding import FP_PREC_DOUBLE_FLOAT
+    cr = synth.licoo2((2, 2, 2))
+    w, e, v = oracle_modes(cr)
+    temps = [300.0, 500.0, 700.0]
+    for dq_mode in (0, 1):
+        ref, acc = oracle.rates4(cr, w, e, v, temps=temps, dq_mode=dq_mode)
+        out, st = run_gpu(lib, cr, w, e, v, temps=temps, dq_mode=dq_mode, precision=FP_PREC_DOUBLE_FLOAT)
+        compare(out.reshape(3, -1), ref, RTOL_FP64)
+        assert np.array_equal(np.array(st["accepted"]), acc)
+    cr = synth.simple_cubic((4, 3, 3))
+    w, e, v = oracle_modes(cr)
+    ref, acc = oracle.rates4(cr, w, e, v)
+    out, st = run_gpu(lib, cr, w, e, v, precision=FP_PREC_DOUBLE_FLOAT, **tiles)
+    compare(out.reshape(1, -1), ref, RTOL_FP64)
+    assert np.array_equal(np.array(st["accepted"]), acc)
