@@ -6,12 +6,18 @@ scalebroad 1.0 -- the configuration the headline metric is quoted on.  A step is
 full-grid rate set: Bose weights, the fused persistent rate kernel (vertex assembly,
 contraction, window, Gaussian, accumulation) and the fixed-order reduction.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|df|mixed] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  `value` is candidate process terms per second with the
 modes resident in HBM; `e2e` is the same metric through the public C-ABI calls with host
 buffers (fp_init + fp_modes + fp_rates4 + fp_free per step); `cpu_baseline` is the FP64
-oracle timed on a bounded sample of the same workload on the host cores.
+oracle timed on a bounded sample of the same workload on the host cores.  The same line
+times the other paths on this workload (`other_precision`, `double_float`,
+`mixed_tensor_cores`, `three_phonon`) and, in `configs`, the other workloads: simple cubic
+4^3, zincblende BAs 12^3 (FP64 and mixed on the full grid), LiCoO2 10x10x6 with 3
+temperatures and diamond 16^3 with 8 (strided q-slices where a full set would exceed
+--budget-s, labelled as extrapolated), each with its error against the oracle on sampled
+modes.  --surrogate, --sweep and --configs print studies instead of the bench line.
 """
 from __future__ import annotations
 
@@ -32,8 +38,9 @@ from paper_2104_04895_gb300 import synth  # noqa: E402
 from paper_2104_04895_gb300.sharding import (balanced_shard, estimate_costs, load_imbalance,  # noqa: E402
                                               max_over_ranks, rank_mask)
 
-FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (recipe nominal; 152 SMs x 2070 MHz x 2 DFMA/clk/SM x 2 = 1.26)
-FP32_PEAK_TFLOPS = 80.5   # 152 SMs x 2070 MHz x 128 FFMA/clk/SM x 2
+# issue rates of the two ALU pipes per SM and clock on sm_103 (GB300): 2 FP64 FMA, 128 FP32 FMA
+DFMA_PER_CLK_SM = 2
+FFMA_PER_CLK_SM = 128
 FLOPS_PER_ACCEPTED_TERM = 25.0  # Gaussian, Bose weights and |W|^2 of one accepted term at one temperature
 
 
@@ -52,6 +59,8 @@ def parse():
     p.add_argument("--no-other", action="store_true", help="skip timing the other precision")
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--surrogate", action="store_true", help="learned-rate study instead of the bench line")
+    p.add_argument("--sweep", action="store_true",
+                   help="learned rates at new temperatures (36 temperatures, 3 anchors) instead of the bench line")
     p.add_argument("--configs", action="store_true",
                    help="per-workload study: time and oracle error of both precisions on workloads 1-5")
     p.add_argument("--budget-s", type=float, default=300.0,
@@ -127,6 +136,24 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def alu_peaks(torch, device_index):
+    """FP64 and FP32 peak TFLOP/s of this GPU from its SM count and maximum SM clock (2 flops per FMA), with the
+    basis as text.  The clock comes from nvidia-smi (clocks.max.sm); without it, 2070 MHz, GB300's maximum."""
+    nsm = torch.cuda.get_device_properties(device_index).multi_processor_count
+    mhz, src = 2070.0, "GB300 maximum SM clock"
+    try:
+        r = subprocess.run(["nvidia-smi", "-i", str(device_index), "--query-gpu=clocks.max.sm",
+                            "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=30)
+        mhz, src = float(r.stdout.strip().splitlines()[0]), "nvidia-smi clocks.max.sm"
+    except (OSError, ValueError, IndexError, subprocess.TimeoutExpired):
+        pass
+    fp64 = nsm * mhz * 1e6 * DFMA_PER_CLK_SM * 2 / 1e12
+    fp32 = nsm * mhz * 1e6 * FFMA_PER_CLK_SM * 2 / 1e12
+    basis = (f"derived: {nsm} SMs x {mhz:.0f} MHz ({src}) x {DFMA_PER_CLK_SM} DFMA or {FFMA_PER_CLK_SM} FFMA "
+             f"per clock and SM x 2 flops")
+    return fp64, fp32, basis
 
 
 def e2e_input_bytes(binding, cr):
@@ -232,6 +259,8 @@ def main():
         return run_reference(args)
     if args.surrogate:
         return run_surrogate(args)
+    if args.sweep:
+        return run_sweep(args)
     if args.configs:
         return run_configs(args)
     import torch
@@ -285,13 +314,14 @@ def main():
     # accumulation of every accepted term at every temperature (Gaussian, Bose weights, |W|^2: 25 flops)
     acc_flops = FLOPS_PER_ACCEPTED_TERM * st["terms_executed"] * nT
     achieved_tflops = (st["flops"] + acc_flops) / (kms * 1e-3) / 1e12
-    peak = FP32_PEAK_TFLOPS if main_prec == binding.FP_PREC_MIXED else FP64_PEAK_TFLOPS
+    fp64_peak, fp32_peak, peak_basis = alu_peaks(torch, local)
+    peak = fp32_peak if main_prec == binding.FP_PREC_MIXED else fp64_peak
     other = None
     if not args.no_other:
         o_ms, o_kms, o_st = time_precision(ctx, binding, torch, cr, other_prec, part, out_other, flush, stream,
                                            args.steps, args.warmup, barrier)
         o_ms = max_over_ranks(o_ms, dist if ws > 1 else None, dev)
-        o_peak = FP64_PEAK_TFLOPS if other_prec == binding.FP_PREC_FP64 else FP32_PEAK_TFLOPS
+        o_peak = fp64_peak if other_prec == binding.FP_PREC_FP64 else fp32_peak
         o_ach = (o_st["flops"] + FLOPS_PER_ACCEPTED_TERM * o_st["terms_executed"] * nT) / (o_kms * 1e-3) / 1e12
         other = {"precision": "fp64" if other_prec == binding.FP_PREC_FP64 else "mixed",
                  "value": cands_step * args.steps / (o_ms * 1e-3), "unit": "process-terms/s",
@@ -354,7 +384,8 @@ def main():
     # the other benchmark workloads, one record each (rank 0 of a single-GPU run)
     configs = None
     if ws == 1 and not args.no_configs and not args.grid:
-        configs = [measure_workload(binding, wl, full_fp64_max_s=args.budget_s) for wl in (1, 3, 4, 5)]
+        configs = [measure_workload(binding, wl, full_max_s=args.budget_s, df_full_max_s=min(60.0, args.budget_s),
+                                    tensor_cores=False) for wl in (1, 3, 4, 5)]
 
     if rank == 0:
         base = None
@@ -392,7 +423,7 @@ def main():
                        "parallelism": part_desc},
             "rel_err_vs_oracle_sampled": rel_err,
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved_tflops / peak, "traffic": None,
+                         "frac": achieved_tflops / peak, "traffic": None, "peak_basis": peak_basis,
                          "pipe": "fp32" if main_prec == binding.FP_PREC_MIXED else "fp64",
                          "kernel_ms": kms, "flops_per_launch": st["flops"] + acc_flops,
                          "flops_vertex": st["flops"], "flops_accumulate": acc_flops},
@@ -479,6 +510,74 @@ def run_surrogate(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sweep(args):
+    """Learned rates at new temperatures against the exact path (one JSON line).
+
+    Output temperatures 300..1000 K every 20 K (36): the exact path needs five temperature-batched rate sets (8, 8,
+    8, 8, 4 temperatures), each timed here on strided q-slices of the grid (or in full when it is short).  The
+    surrogate takes exact rates of every mode at 300, 650 and 1000 K (one batched set) and of a seeded 15 % of the
+    pairs {q, -q} at the 36 temperatures, trains, predicts and falls back per bin.  Its realised error is measured
+    on exact rates of a seeded sample of 200 predicted modes at all 36 temperatures."""
+    from paper_2104_04895_gb300 import binding
+    cr = synth.workload(args.workload)
+    if args.grid:
+        cr = cr.with_grid(args.grid)
+    N, nb = cr.nq, cr.nb
+    temps = [float(t) for t in np.arange(300.0, 1000.0 + 1e-9, 20.0)]
+    anchors = [300.0, 650.0, 1000.0]
+    full_exec = 3.0 * N * N * nb ** 3 * nb * (N + _self_conjugate(cr.grid)) / 2.0
+    prec = binding.FP_PREC_MIXED
+    with binding.Context.from_crystal(cr) as ctx:
+        ctx.modes(copy=False)
+        ctx.autotune(temps[:8], cr.scalebroad, precision=prec)
+        t_exact, parts = 0.0, []
+        for i in range(0, len(temps), 8):
+            chunk = temps[i:i + 8]
+            probe = np.zeros(N * nb, np.uint8)
+            probe[nb:2 * nb] = 1
+            _, st = ctx.rates4(chunk, cr.scalebroad, precision=prec, mode_mask=probe, no_graph=1)
+            est = st["ms"] * 1e-3 * full_exec / st["candidates_executed"]
+            if est <= args.budget_s:
+                _, st = ctx.rates4(chunk, cr.scalebroad, precision=prec)
+                secs = st["ms"] * 1e-3
+            else:
+                m = max(2, int(np.ceil(N * est / ((N + _self_conjugate(cr.grid)) / 2.0) / 20.0)))
+                ext = []
+                for k in (0, m // 3, (2 * m) // 3):
+                    _, st = ctx.rates4(chunk, cr.scalebroad, precision=prec, mode_mask=_slice_mask(cr, m, k),
+                                       no_graph=1)
+                    ext.append(st["ms"] * 1e-3 * full_exec / st["candidates_executed"])
+                secs = float(np.mean(ext))
+            parts.append(secs)
+            t_exact += secs
+        t0 = time.perf_counter()
+        rates, used, rep = ctx.surrogate_sweep(anchors, temps, cr.scalebroad, seed=args.seed)
+        t_sur = time.perf_counter() - t0
+        pred_modes = np.nonzero(((used == 0) & (rates > 0)).any(axis=0).reshape(-1))[0]
+        rel = np.array([])
+        if pred_modes.size:
+            rng = np.random.Generator(np.random.PCG64(args.seed + 1))
+            pick = np.sort(rng.choice(pred_modes, size=min(200, pred_modes.size), replace=False))
+            mask = np.zeros(N * nb, np.uint8)
+            mask[pick] = 1
+            ex = np.concatenate([ctx.rates4(temps[i:i + 8], cr.scalebroad, precision=prec, mode_mask=mask,
+                                            no_graph=1)[0].reshape(-1, N * nb)[:, pick] for i in range(0, len(temps), 8)])
+            pr = rates.reshape(len(temps), -1)[:, pick]
+            ok = (ex > 0) & (used.reshape(len(temps), -1)[:, pick] == 0)
+            rel = np.abs(pr[ok] - ex[ok]) / ex[ok]
+    pos = rates > 0
+    line = {"metric": "four-phonon rates at new temperatures: surrogate vs exact (mixed, temperature-batched)",
+            "workload": f"{cr.name} {cr.grid[0]}x{cr.grid[1]}x{cr.grid[2]} nb={nb}",
+            "temperatures": len(temps), "anchors": anchors,
+            "exact_s": t_exact, "exact_batches_s": parts, "surrogate_s": t_sur, "speedup": t_exact / t_sur,
+            "exact_share": float(used[pos].mean()), "predicted_modes": int(pred_modes.size),
+            "predicted_rel_err_sampled": {"n": int(rel.size), "median": float(np.median(rel)) if rel.size else None,
+                                          "p90": float(np.quantile(rel, 0.9)) if rel.size else None,
+                                          "max": float(rel.max()) if rel.size else None},
+            "report": rep}
+    print(json.dumps(line), flush=True)
+
+
 def _self_conjugate(grid):
     """Number of grid points q with -q = q (mod the grid)."""
     n = 1
@@ -494,11 +593,14 @@ def _slice_mask(cr, m, k):
     return mask.reshape(-1)
 
 
-def measure_workload(binding, wl, budget_slice_s=20.0, full_fp64_max_s=300.0, oracle_max_s=150.0):
+def measure_workload(binding, wl, budget_slice_s=10.0, full_max_s=300.0, oracle_max_s=150.0, df_full_max_s=None,
+                     tensor_cores=True):
     """Seconds per full-grid rate set of workload `wl` in each precision, and errors on sampled modes.
 
-    A precision whose full rate set is estimated (from a one-q probe) to stay under `full_fp64_max_s` is timed on
-    the whole grid.  Otherwise three strided q-slices (q = k mod m, all branches) are timed and scaled to the grid
+    An FP64 or mixed rate set estimated (from a one-q probe) to stay under `full_max_s` is timed on the whole grid,
+    a double-float one under `df_full_max_s` (default: the same), and the tensor-core option (nb = 6 only) when
+    `tensor_cores` is set and the mixed set ran in full.  Otherwise three strided q-slices (q = k mod m, all
+    branches) of about `budget_slice_s` each are timed and scaled to the grid
     by the candidates the kernel screened (time reversal evaluates (N + self-conjugate points) / 2 points of a full
     grid); the spread of the three gives the sampling uncertainty.  The GPU takes the oracle's modes, so the error
     against the oracle on a ruled mode sample (lowest positive frequency and one seeded mode) is a strict one; the
@@ -530,7 +632,8 @@ def measure_workload(binding, wl, budget_slice_s=20.0, full_fp64_max_s=300.0, or
             est = t_rep * full_exec / (nb * 3.0 * N * N * nb ** 3)
             smask = np.zeros(N * nb, np.uint8)
             smask[sample] = 1
-            if est <= full_fp64_max_s:
+            limit = df_full_max_s if (name == "double_float" and df_full_max_s is not None) else full_max_s
+            if est <= limit:
                 out, st = ctx.rates4(cr.temps, cr.scalebroad, precision=prec)
                 secs = st["ms"] * 1e-3
                 rec = {"s_per_rate_set": secs, "terms_per_s": cands / secs, "timing": "full grid, one rate set",
@@ -552,7 +655,7 @@ def measure_workload(binding, wl, budget_slice_s=20.0, full_fp64_max_s=300.0, or
                 outs[name] = out.reshape(nT, -1)[:, sample]
             rec["tile"] = st["tile"]
             res[name] = rec
-        if nb == 6 and res["mixed"]["timing"].startswith("full grid"):
+        if tensor_cores and nb == 6 and res["mixed"]["timing"].startswith("full grid"):
             out, st = ctx.rates4(cr.temps, cr.scalebroad, precision=binding.FP_PREC_MIXED, tensor_cores=1)
             secs = st["ms"] * 1e-3
             res["mixed_tensor_cores"] = {"s_per_rate_set": secs, "terms_per_s": cands / secs, "tile": st["tile"],
@@ -579,7 +682,7 @@ def run_configs(args):
     """One JSON line per workload (see measure_workload)."""
     from paper_2104_04895_gb300 import binding
     for wl in (1, 2, 3, 4, 5):
-        print(json.dumps(measure_workload(binding, wl, full_fp64_max_s=args.budget_s)), flush=True)
+        print(json.dumps(measure_workload(binding, wl, full_max_s=args.budget_s)), flush=True)
 
 
 if __name__ == "__main__":

@@ -382,6 +382,23 @@ void fp_surrogate_default_opts(fp_surrogate_opts* opts);
 int fp_surrogate_fit(fp_ctx* ctx, int nT, const double* T, double scalebroad, const fp_surrogate_opts* opts,
                      fp_surrogate_report* report);
 
+/*
+ * Learned rates at new temperatures (the paper has no learned component): a temperature sweep with more
+ * temperatures than one batched evaluation takes (8).  Exact rates (fp_rates4) of every mode at nA anchor
+ * temperatures (one batched evaluation, 1 <= nA <= 8) and exact rates of a seeded train_frac share of the pairs
+ * {q, -q} at the nT output temperatures (1 <= nT <= 64, evaluated 8 at a time) train the 3 x 128 tanh network on
+ * the GPU (the same hand-written kernels as fp_surrogate_fit) to map, per (mode, T), the mode's anchor log rates,
+ * log(T/300), log n0(T), w/w_max and a branch one-hot to log(rate(T)).  Exact rates of a further holdout_frac share
+ * of the pairs judge it per bin (branch x frequency quartile) with the rule of fp_surrogate_fit; every other bin is
+ * evaluated exactly at the output temperatures.  Every trained, held-out or fallback entry keeps its exact rate.
+ *   rates: host nT x N x nb (ps^-1); used_exact: host nT x N x nb, 1 = exact, 0 = predicted; either may be NULL.
+ * opts as for fp_surrogate_fit (NULL = defaults).  report (nullable): ms_exact covers the anchor and subset
+ * evaluations.  FP_EINVAL for nA or nT out of range or temperatures <= 0; FP_ESTATE before the modes.
+ */
+int fp_surrogate_sweep(fp_ctx* ctx, int nA, const double* T_anchor, int nT, const double* T, double scalebroad,
+                       const fp_surrogate_opts* opts, double* rates, unsigned char* used_exact,
+                       fp_surrogate_report* report);
+
 /* Rates of the last fp_surrogate_fit (host, nT x N x nb) and per-entry flags: 1 = exact, 0 = predicted. */
 int fp_surrogate_rates(fp_ctx* ctx, double* rates, unsigned char* used_exact);
 

@@ -62,7 +62,7 @@ class fp_stats(ctypes.Structure):
 EXPORTS = ["fp_version", "fp_default_opts", "fp_init", "fp_set_stream", "fp_modes", "fp_set_modes", "fp_rates4",
            "fp_rates4_channels", "fp_rates4_nu", "fp_set_fc3", "fp_rates3", "fp_kappa_rta", "fp_rates4_irreducible", "fp_star_table", "fp_rates4_device", "fp_rates4_noalloc", "fp_autotune", "fp_phase3", "fp_phase4", "fp_mlp_params_size",
            "fp_mlp_loss_grad", "fp_surrogate_default_opts", "fp_surrogate_fit", "fp_surrogate_rates", "fp_free",
-           "fp_last_error", "fp_phase_space4", "fp_write_fc4", "fp_read_fc4", "fp_write_fc3", "fp_read_fc3"]
+           "fp_last_error", "fp_phase_space4", "fp_surrogate_sweep", "fp_write_fc4", "fp_read_fc4", "fp_write_fc3", "fp_read_fc3"]
 
 
 class fp_surrogate_opts(ctypes.Structure):
@@ -160,6 +160,10 @@ def load(path: str | None = None):
                                    ctypes.POINTER(fp_surrogate_report)]
     L.fp_surrogate_fit.restype = ctypes.c_int
     L.fp_surrogate_rates.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_ubyte)]
+    L.fp_surrogate_sweep.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int, dp, ctypes.c_double,
+                                     ctypes.POINTER(fp_surrogate_opts), dp, ctypes.POINTER(ctypes.c_ubyte),
+                                     ctypes.POINTER(fp_surrogate_report)]
+    L.fp_surrogate_sweep.restype = ctypes.c_int
     L.fp_surrogate_rates.restype = ctypes.c_int
     L.fp_phase_space4.argtypes = [vp, ctypes.c_int, dp, ctypes.c_double, ctypes.POINTER(fp_rates_opts), ctypes.c_int,
                                   dp, dp, dp]
@@ -445,6 +449,24 @@ class Context:
                                                        ctypes.byref(rep)))
         self._sur_nT = len(T)
         return rep.as_dict()
+
+    def surrogate_sweep(self, anchors, temps, scalebroad=1.0, **sopts):
+        """Learned rates at new temperatures (fp_surrogate_sweep): (rates (nT, N, nb), used_exact (nT, N, nb),
+        report dict) from exact rates at the anchor temperatures and on a seeded subset at `temps`."""
+        A = np.ascontiguousarray(anchors, np.float64).reshape(-1)
+        T = np.ascontiguousarray(temps, np.float64).reshape(-1)
+        so = fp_surrogate_opts()
+        self.L.fp_surrogate_default_opts(ctypes.byref(so))
+        for k, v in sopts.items():
+            setattr(so, k, v)
+        rep = fp_surrogate_report()
+        r = np.zeros((len(T), self.N, self.nb))
+        u = np.zeros((len(T), self.N, self.nb), np.uint8)
+        _check(self.L, self.h, self.L.fp_surrogate_sweep(self.h, len(A), _dp(A), len(T), _dp(T), float(scalebroad),
+                                                         ctypes.byref(so), _dp(r),
+                                                         u.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)),
+                                                         ctypes.byref(rep)))
+        return r, u, rep.as_dict()
 
     def surrogate_rates(self):
         """Rates of the last surrogate fit (nT, N, nb) and the exact-evaluation flags (same shape)."""

@@ -113,6 +113,23 @@ int max_ctas_per_sm(int precision, int nb, int nT, int threads, size_t smem, boo
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess) return 0;
+  if (tc) {
+    // For the tensor-core kernel the occupancy query reports one CTA per SM although its registers and shared
+    // memory fit two (ncu's launch limits agree: two by registers, two by shared memory), and two use 64 of the
+    // 512 TMEM columns.  Size the persistent grid from the registers and shared memory; a CTA that cannot be
+    // resident yet starts later and finds fewer work items.
+    cudaFuncAttributes fa;
+    int dev = 0, regs_sm = 0, smem_sm = 0;
+    if (cudaFuncGetAttributes(&fa, k) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess) {
+      const long long warp_regs = ((long long)fa.numRegs * 32 + 255) / 256 * 256;
+      const long long by_regs = regs_sm / (warp_regs * ((threads + 31) / 32));
+      const long long by_smem = smem_sm / ((long long)smem + fa.sharedSizeBytes + 1024);
+      const int est = (int)std::min(by_regs, by_smem);
+      if (est > n) n = std::min(est, 2);
+    }
+  }
   return n;
 }
 
@@ -221,6 +238,20 @@ int plan_rates(fp_ctx* c, const fp_rates_opts& o, int nT, Selection& sel, size_t
   if (o.k1_tile <= 0 && partial_budget)
     while (t1 < N && part_bytes(t1) > partial_budget) t1 = t1 < 8 ? t1 + 1 : t1 + t1 / 4;
   if (t1 > N) t1 = N;
+  // the kernel counts an item's accepted terms in 32 bits: at most 6 per (q', q'', j''') of a row, times the
+  // row's multiplicity 2, over the tile's t1 q' values
+  const double max_t1 = 4294967295.0 / (12.0 * (double)N * nb);
+  if (max_t1 < 1.0) {
+    *err = "grid too large for the per-item counters";
+    return FP_EINVAL;
+  }
+  if ((double)t1 > max_t1) {
+    if (o.k1_tile > 0) {
+      *err = "k1_tile too large for the per-item counters of this grid";
+      return FP_EINVAL;
+    }
+    t1 = (int)max_t1;
+  }
   if (partial_budget && part_bytes(t1) > partial_budget) {
     *err = "per-item partial sums do not fit the scratch";
     return FP_EINVAL;

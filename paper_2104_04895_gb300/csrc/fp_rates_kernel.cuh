@@ -529,8 +529,6 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
   const int rjj = tid / NB2, rj1 = (tid / NB) % NB, rc = tid % NB;
   const size_t NM = (size_t)N * NB;
   const bool f32_sigma = !kF64 && a.dq_mode == 0;
-  // accepted terms (weighted by the rows' multiplicities), vertex entries formed, accepted terms evaluated
-  unsigned long long cnt0 = 0, cnt1 = 0, cnt2 = 0, nwf = 0, nte = 0;
   constexpr int S = acc_slots(NB);
   const int lane = tid & 31;
   const int qbase = (tid >> 5) * kQCap;
@@ -650,7 +648,9 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
       }
     };
 
-    unsigned icnt = 0;  // accepted terms of this item (the thread's row)
+    // counters of this item, flushed to the launch totals at its end: accepted terms per process, weighted by the
+    // row's multiplicity (the evaluated terms are these over the multiplicity), and vertex entries formed
+    unsigned cnt0 = 0, cnt1 = 0, cnt2 = 0, nwf = 0;
     const int k1_begin = tile * a.t1;
     const int k1_end = min(N, k1_begin + a.t1);
     // unit-vertex (phase-space) mode: q' on a stride, every q'' in one ordering, |W|^2 = 1
@@ -1065,8 +1065,6 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
               cnt0 += row_mult * __popc(accm & 0x09u);
               cnt1 += row_mult * __popc(accm & 0x12u);
               cnt2 += row_mult * __popc(accm & 0x24u);
-              nte += __popc(accm);
-              icnt += __popc(accm);
             }
             // entries with an accepted candidate, one per lane at most, in lane order
             const unsigned bal = __ballot_sync(0xffffffffu, accm != 0);
@@ -1128,8 +1126,6 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
                 cnt0 += row_mult * __popc(accm & 0x09u);
                 cnt1 += row_mult * __popc(accm & 0x12u);
                 cnt2 += row_mult * __popc(accm & 0x24u);
-                nte += __popc(accm);
-                icnt += __popc(accm);
                 C Wv = cmk<R>(unit ? 1 : 0, 0);
                 if (!unit) {
                   ++nwf;
@@ -1225,10 +1221,12 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
       a.partial[(size_t)item * J * nT + o] = sum;
     }
     __syncthreads();
+    // accepted terms this row evaluated (the weighted counts over the row's multiplicity)
+    const unsigned nte = row_mult ? (unsigned)(((unsigned long long)cnt0 + cnt1 + cnt2) / row_mult) : 0u;
     if (a.item_counts) {
       // accepted terms per j0 of the item: the rows jj * nb^2 .. (jj + 1) * nb^2 - 1, in row order
       unsigned long long* sCnt = reinterpret_cast<unsigned long long*>(sRed);  // reuses the reduction buffer
-      sCnt[tid] = icnt;
+      sCnt[tid] = nte;
       __syncthreads();
       for (int jj = tid; jj < J; jj += nthr) {
         unsigned long long sum = 0;
@@ -1237,21 +1235,22 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
       }
       __syncthreads();
     }
-  }
-  // accepted counts and vertex entries formed
-  for (int off = 16; off > 0; off >>= 1) {
-    cnt0 += __shfl_down_sync(0xffffffffu, cnt0, off);
-    cnt1 += __shfl_down_sync(0xffffffffu, cnt1, off);
-    cnt2 += __shfl_down_sync(0xffffffffu, cnt2, off);
-    nwf += __shfl_down_sync(0xffffffffu, nwf, off);
-    nte += __shfl_down_sync(0xffffffffu, nte, off);
-  }
-  if ((tid & 31) == 0) {
-    if (cnt0) atomicAdd(a.counts + 0, cnt0);
-    if (cnt1) atomicAdd(a.counts + 1, cnt1);
-    if (cnt2) atomicAdd(a.counts + 2, cnt2);
-    if (nwf) atomicAdd(a.counts + 3, nwf);
-    if (nte) atomicAdd(a.counts + 4, nte);
+    // the item's counters into the launch totals: warp sums, one atomic per counter and warp
+    unsigned long long c0 = cnt0, c1 = cnt1, c2 = cnt2, cw = nwf, ct = nte;
+    for (int off = 16; off > 0; off >>= 1) {
+      c0 += __shfl_down_sync(0xffffffffu, c0, off);
+      c1 += __shfl_down_sync(0xffffffffu, c1, off);
+      c2 += __shfl_down_sync(0xffffffffu, c2, off);
+      cw += __shfl_down_sync(0xffffffffu, cw, off);
+      ct += __shfl_down_sync(0xffffffffu, ct, off);
+    }
+    if (lane == 0) {
+      if (c0) atomicAdd(a.counts + 0, c0);
+      if (c1) atomicAdd(a.counts + 1, c1);
+      if (c2) atomicAdd(a.counts + 2, c2);
+      if (cw) atomicAdd(a.counts + 3, cw);
+      if (ct) atomicAdd(a.counts + 4, ct);
+    }
   }
   if constexpr (TC) {
     tc::fence_before_sync();

@@ -151,6 +151,23 @@ __global__ void features_kernel(const double* omega, const double* vel, const do
   x[12 + nb] = (float)log(fabs(wp4[r]) + 1e-30);
 }
 
+// Features of the temperature sweep per (output temperature, mode): [log anchor rate (nA), log(T/300), log n0(T),
+// w/wmax, branch one-hot (nb)] -> F = nA + 3 + nb columns; rows r = t * N*nb + m.
+__global__ void sweep_features_kernel(const double* anchor, const double* omega, const double* T, int nm, int nb,
+                                      int nT, int nA, double wmax, float* X) {
+  const int F = nA + 3 + nb;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nm * nT) return;
+  const int t = r / nm, m = r % nm;
+  float* x = X + (size_t)r * F;
+  for (int k = 0; k < nA; ++k) x[k] = (float)log(fmax(anchor[(size_t)k * nm + m], 1e-300));
+  const double w = omega[m];
+  x[nA] = (float)log(T[t] / 300.0);
+  x[nA + 1] = (float)log((w > 0.0 ? 1.0 / expm1(kHbar * w / (kBoltzmann * T[t])) : 0.0) + 1e-30);
+  x[nA + 2] = (float)(w / wmax);
+  for (int j = 0; j < nb; ++j) x[nA + 3 + j] = (j == m % nb) ? 1.0f : 0.0f;
+}
+
 // column mean and standard deviation over the listed rows (one thread per column, fixed order)
 __global__ void col_stats_kernel(const float* X, int F, const int* rows, int n, float* mean, float* stdv) {
   int f = blockIdx.x * blockDim.x + threadIdx.x;
@@ -395,6 +412,29 @@ std::vector<float> init_params(int F, unsigned long long seed) {
   return p;
 }
 
+// The pairs {q, -q} of the grid with all their positive-frequency branches (mode indices q * nb + j), one entry per
+// pair, by smallest q.  Subsets are drawn in these units because the rate path evaluates a pair at once (time
+// reversal), so the exact share of the cost is the share of pairs drawn.
+std::vector<std::vector<int>> pair_units(const int grid[3], int nb, const std::vector<double>& om) {
+  const int N = grid[0] * grid[1] * grid[2];
+  std::vector<std::vector<int>> units;
+  std::vector<char> seen(N, 0);
+  for (int q = 0; q < N; ++q) {
+    if (seen[q]) continue;
+    const int g0 = q / (grid[1] * grid[2]), g1 = (q / grid[2]) % grid[1], g2 = q % grid[2];
+    const int p = (((grid[0] - g0) % grid[0]) * grid[1] + (grid[1] - g1) % grid[1]) * grid[2] +
+                  (grid[2] - g2) % grid[2];
+    seen[q] = seen[p] = 1;
+    std::vector<int> u;
+    const int members[2] = {q, p};
+    for (int k = 0; k < (p == q ? 1 : 2); ++k)
+      for (int j = 0; j < nb; ++j)
+        if (om[(size_t)members[k] * nb + j] > 0.0) u.push_back(members[k] * nb + j);
+    if (!u.empty()) units.push_back(u);
+  }
+  return units;
+}
+
 }  // namespace
 }  // namespace fp
 
@@ -570,25 +610,8 @@ extern "C" int fp_surrogate_fit(fp_ctx* c, int nT, const double* T, double sb, c
   std::vector<int> pos;
   for (int m = 0; m < nm; ++m)
     if (om[m] > 0.0) pos.push_back(m);
-  // training and held-out modes are drawn as whole pairs {q, -q} with all their branches: the rate path evaluates
-  // a pair at once (time reversal), so the exact share of the cost is the share of pairs drawn
-  std::vector<std::vector<int>> units;
-  {
-    std::vector<char> seen(c->N, 0);
-    for (int q = 0; q < c->N; ++q) {
-      if (seen[q]) continue;
-      const int g0 = q / (c->grid[1] * c->grid[2]), g1 = (q / c->grid[2]) % c->grid[1], g2 = q % c->grid[2];
-      const int p = (((c->grid[0] - g0) % c->grid[0]) * c->grid[1] + (c->grid[1] - g1) % c->grid[1]) * c->grid[2] +
-                    (c->grid[2] - g2) % c->grid[2];
-      seen[q] = seen[p] = 1;
-      std::vector<int> u;
-      const int members[2] = {q, p};
-      for (int k = 0; k < (p == q ? 1 : 2); ++k)
-        for (int j = 0; j < nb; ++j)
-          if (om[(size_t)members[k] * nb + j] > 0.0) u.push_back(members[k] * nb + j);
-      if (!u.empty()) units.push_back(u);
-    }
-  }
+  // training and held-out modes: whole pairs {q, -q} with all their branches
+  std::vector<std::vector<int>> units = fp::pair_units(c->grid, nb, om);
   SplitMix64 rng{so.seed};
   for (size_t i = units.size(); i > 1; --i) std::swap(units[i - 1], units[rng.next() % i]);
   const int u_train = std::max(1, (int)std::ceil(so.train_frac * units.size()));
@@ -882,5 +905,288 @@ extern "C" int fp_surrogate_rates(fp_ctx* c, double* rates, unsigned char* used_
   if (c->sur_nT == 0) return sfail(c, FP_ESTATE, "fp_surrogate_rates: call fp_surrogate_fit first");
   if (rates) std::memcpy(rates, c->sur_rates.data(), c->sur_rates.size() * sizeof(double));
   if (used_exact) std::memcpy(used_exact, c->sur_used.data(), c->sur_used.size());
+  return FP_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Learned rates at new temperatures (fp_surrogate_sweep)
+extern "C" int fp_surrogate_sweep(fp_ctx* c, int nA, const double* TA, int nT, const double* T, double sb,
+                                  const fp_surrogate_opts* user, double* rates, unsigned char* used_exact,
+                                  fp_surrogate_report* rep) {
+  using namespace fp;
+  if (!c) return FP_EINVAL;
+  fp_surrogate_opts so;
+  fp_surrogate_default_opts(&so);
+  if (user) so = *user;
+  if (!c->have_modes) return sfail(c, FP_ESTATE, "fp_surrogate_sweep: call fp_modes or fp_set_modes first");
+  if (nA < 1 || nA > kMaxT || !TA) return sfail(c, FP_EINVAL, "fp_surrogate_sweep: nA must be in [1, 8]");
+  if (nT < 1 || nT > 64 || !T) return sfail(c, FP_EINVAL, "fp_surrogate_sweep: nT must be in [1, 64]");
+  for (int i = 0; i < nA; ++i)
+    if (!(TA[i] > 0.0) || !std::isfinite(TA[i])) return sfail(c, FP_EINVAL, "fp_surrogate_sweep: temperatures > 0");
+  for (int i = 0; i < nT; ++i)
+    if (!(T[i] > 0.0) || !std::isfinite(T[i])) return sfail(c, FP_EINVAL, "fp_surrogate_sweep: temperatures > 0");
+  if (!(so.train_frac > 0.0) || !(so.holdout_frac > 0.0) || so.train_frac + so.holdout_frac > 1.0 ||
+      !(so.tol > 0.0) || so.epochs < 1 || so.batch < 1 || !(so.lr > 0.0))
+    return sfail(c, FP_EINVAL, "fp_surrogate_sweep: bad options");
+  const double t_start = now_ms();
+  SG_CUDA(c, cudaSetDevice(c->device));
+  cudaStream_t s = c->stream;
+  const int nb = c->nb, nm = c->N * nb, F = nA + 3 + nb;
+  const size_t rows_all = (size_t)nm * nT;
+
+  std::vector<double> om(nm);
+  SG_CUDA(c, cudaMemcpyAsync(om.data(), c->d_omega, nm * sizeof(double), cudaMemcpyDeviceToHost, s));
+  SG_CUDA(c, cudaStreamSynchronize(s));
+  std::vector<int> pos;
+  for (int m = 0; m < nm; ++m)
+    if (om[m] > 0.0) pos.push_back(m);
+  // training and held-out modes: whole pairs {q, -q} with all their branches
+  std::vector<std::vector<int>> units = fp::pair_units(c->grid, nb, om);
+  SplitMix64 rng{so.seed};
+  for (size_t i = units.size(); i > 1; --i) std::swap(units[i - 1], units[rng.next() % i]);
+  const int u_train = std::max(1, (int)std::ceil(so.train_frac * units.size()));
+  const int u_hold = std::max(1, (int)std::ceil(so.holdout_frac * units.size()));
+  if (u_train + u_hold > (int)units.size()) return sfail(c, FP_EINVAL, "fp_surrogate_sweep: too few modes");
+  std::vector<unsigned char> role(nm, 0);  // 1 train, 2 holdout, 3 fallback
+  int n_train = 0, n_hold = 0;
+  for (int i = 0; i < u_train + u_hold; ++i)
+    for (int m : units[i]) {
+      role[m] = i < u_train ? 1 : 2;
+      (i < u_train ? n_train : n_hold) += 1;
+    }
+
+  // exact rates: every mode at the anchors; the training and held-out modes at the output temperatures
+  double t0 = now_ms();
+  fp_rates_opts ro;
+  fp_default_opts(&ro);
+  ro.precision = so.precision;
+  std::vector<double> anchor((size_t)nA * nm);
+  int rc = fp_rates4(c, nA, TA, sb, &ro, anchor.data(), nullptr);
+  if (rc) return rc;
+  auto exact_at = [&](const std::vector<unsigned char>& mk, std::vector<double>& dst) -> int {
+    std::vector<double> tmp((size_t)kMaxT * nm);
+    fp_rates_opts o = ro;
+    o.mode_mask = mk.data();
+    for (int t0b = 0; t0b < nT; t0b += kMaxT) {
+      const int nc = std::min(kMaxT, nT - t0b);
+      const int r = fp_rates4(c, nc, T + t0b, sb, &o, tmp.data(), nullptr);
+      if (r) return r;
+      std::memcpy(dst.data() + (size_t)t0b * nm, tmp.data(), (size_t)nc * nm * sizeof(double));
+    }
+    return FP_OK;
+  };
+  std::vector<unsigned char> mask(nm, 0);
+  for (int m = 0; m < nm; ++m) mask[m] = role[m] ? 1 : 0;
+  std::vector<double> exact(rows_all, 0.0);
+  if ((rc = exact_at(mask, exact))) return rc;
+  const double ms_exact = now_ms() - t0;
+
+  // features on the device
+  t0 = now_ms();
+  double *dA = nullptr, *dT = nullptr;
+  float *dX = nullptr, *dY = nullptr, *dmean = nullptr, *dstd = nullptr;
+  int* drows = nullptr;
+  Net net;
+  auto cleanup = [&]() {
+    cudaFree(dA);
+    cudaFree(dT);
+    cudaFree(dX);
+    cudaFree(dY);
+    cudaFree(dmean);
+    cudaFree(dstd);
+    cudaFree(drows);
+    net_free(net);
+  };
+#define SW_TRY(call)                                                                                          \
+  do {                                                                                                        \
+    cudaError_t e_ = (call);                                                                                  \
+    if (e_ != cudaSuccess) {                                                                                  \
+      cleanup();                                                                                              \
+      return sfail(c, e_ == cudaErrorMemoryAllocation ? FP_ENOMEM : FP_ECUDA,                                 \
+                   std::string(#call) + ": " + cudaGetErrorString(e_));                                       \
+    }                                                                                                         \
+  } while (0)
+  std::vector<int> train_rows;
+  for (int m = 0; m < nm; ++m) {
+    if (role[m] != 1) continue;
+    bool anchors_ok = true;
+    for (int k = 0; k < nA; ++k) anchors_ok = anchors_ok && anchor[(size_t)k * nm + m] > 0.0;
+    for (int t = 0; t < nT && anchors_ok; ++t)
+      if (exact[(size_t)t * nm + m] > 0.0) train_rows.push_back(t * nm + m);
+  }
+  if (train_rows.empty()) return sfail(c, FP_EINVAL, "fp_surrogate_sweep: no training rates > 0");
+  const int Bmax = std::max(so.batch, 4096);
+  SW_TRY(dalloc(&dA, (size_t)nA * nm));
+  SW_TRY(dalloc(&dT, (size_t)nT));
+  SW_TRY(dalloc(&dX, rows_all * F));
+  SW_TRY(dalloc(&dY, rows_all));
+  SW_TRY(dalloc(&dmean, F));
+  SW_TRY(dalloc(&dstd, F));
+  SW_TRY(dalloc(&drows, std::max(rows_all, (size_t)Bmax)));
+  SW_TRY(net_alloc(net, F, Bmax));
+  SW_TRY(cudaMemcpyAsync(dA, anchor.data(), anchor.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  SW_TRY(cudaMemcpyAsync(dT, T, nT * sizeof(double), cudaMemcpyHostToDevice, s));
+  double wmax = 0.0;
+  for (double w : om) wmax = std::max(wmax, w);
+  sweep_features_kernel<<<(unsigned)((rows_all + 255) / 256), 256, 0, s>>>(dA, c->d_omega, dT, nm, nb, nT, nA, wmax,
+                                                                          dX);
+  SW_TRY(cudaGetLastError());
+  SW_TRY(cudaMemcpyAsync(drows, train_rows.data(), train_rows.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  col_stats_kernel<<<1, 64, 0, s>>>(dX, F, drows, (int)train_rows.size(), dmean, dstd);
+  normalize_kernel<<<(unsigned)((rows_all * F + 255) / 256), 256, 0, s>>>(dX, F, (long long)rows_all, dmean, dstd);
+  std::vector<float> y(rows_all, 0.f);
+  for (size_t r = 0; r < rows_all; ++r)
+    if (exact[r] > 0.0) y[r] = (float)std::log(exact[r]);
+  SW_TRY(cudaMemcpyAsync(dY, y.data(), rows_all * sizeof(float), cudaMemcpyHostToDevice, s));
+  SW_TRY(cudaStreamSynchronize(s));
+  const double ms_features = now_ms() - t0;
+
+  // training: Adam on minibatches, rows reshuffled every epoch
+  t0 = now_ms();
+  {
+    std::vector<float> p0 = init_params(F, so.seed);
+    SW_TRY(cudaMemcpyAsync(net.p, p0.data(), p0.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    SW_TRY(cudaMemsetAsync(net.m, 0, p0.size() * sizeof(float), s));
+    SW_TRY(cudaMemsetAsync(net.v, 0, p0.size() * sizeof(float), s));
+  }
+  const int P = (int)nparams(F);
+  const int nrows = (int)train_rows.size();
+  const int B = std::max(1, std::min(so.batch, std::max(32, nrows / 8)));
+  std::vector<int> order(train_rows);
+  int step = 0;
+  const float b1 = 0.9f, b2 = 0.999f;
+  for (int ep = 0; ep < so.epochs; ++ep) {
+    for (size_t i = order.size(); i > 1; --i) std::swap(order[i - 1], order[rng.next() % i]);
+    SW_TRY(cudaMemcpyAsync(drows, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    for (int b0 = 0; b0 + B <= nrows; b0 += B) {
+      gather_kernel<<<(B * F + 255) / 256, 256, 0, s>>>(dX, F, drows + b0, B, net.X, dY, net.t);
+      SW_TRY(net_forward(net, B, s));
+      SW_TRY(net_backward(net, B, s));
+      ++step;
+      const float c1 = 1.f - std::pow(b1, (float)step), c2 = 1.f - std::pow(b2, (float)step);
+      adam_kernel<<<(P + 255) / 256, 256, 0, s>>>(net.p, net.g, net.m, net.v, P, (float)so.lr, b1, b2, 1e-8f, c1, c2);
+    }
+  }
+  float final_loss = 0.f;
+  SW_TRY(cudaMemcpyAsync(&final_loss, net.loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+  SW_TRY(cudaStreamSynchronize(s));
+  const double ms_train = now_ms() - t0;
+
+  // prediction for every (temperature, mode) row
+  t0 = now_ms();
+  double* dpred = nullptr;
+  SW_TRY(dalloc(&dpred, rows_all));
+  std::vector<int> all(rows_all);
+  std::iota(all.begin(), all.end(), 0);
+  SW_TRY(cudaMemcpyAsync(drows, all.data(), rows_all * sizeof(int), cudaMemcpyHostToDevice, s));
+  for (size_t r0 = 0; r0 < rows_all; r0 += Bmax) {
+    const int nr = (int)std::min((size_t)Bmax, rows_all - r0);
+    gather_kernel<<<(nr * F + 255) / 256, 256, 0, s>>>(dX, F, drows + r0, nr, net.X, nullptr, nullptr);
+    SW_TRY(net_forward(net, nr, s));
+    exp_kernel<<<(nr + 255) / 256, 256, 0, s>>>(net.y, nr, drows + r0, (int)rows_all, dpred);
+  }
+  std::vector<double> pred(rows_all);
+  SW_TRY(cudaMemcpyAsync(pred.data(), dpred, rows_all * sizeof(double), cudaMemcpyDeviceToHost, s));
+  SW_TRY(cudaStreamSynchronize(s));
+  cudaFree(dpred);
+  const double ms_predict = now_ms() - t0;
+
+  // held-out error per bin (branch x frequency quartile): the rule of fp_surrogate_fit
+  std::vector<double> wsorted;
+  for (int m : pos) wsorted.push_back(om[m]);
+  std::sort(wsorted.begin(), wsorted.end());
+  double qcut[3];
+  for (int k = 0; k < 3; ++k) qcut[k] = wsorted[(size_t)((k + 1) * wsorted.size() / 4)];
+  auto bin_of = [&](int m) {
+    int qb = 0;
+    while (qb < 3 && om[m] >= qcut[qb]) ++qb;
+    return (m % nb) * 4 + qb;
+  };
+  const int nbins = nb * 4;
+  std::vector<double> bin_err(nbins, 0.0), bin_err2(nbins, 0.0), errs;
+  std::vector<int> bin_cnt(nbins, 0);
+  for (int m = 0; m < nm; ++m) {
+    if (role[m] != 2) continue;
+    for (int t = 0; t < nT; ++t) {
+      const size_t r = (size_t)t * nm + m;
+      if (!(exact[r] > 0.0)) continue;
+      const double e = std::fabs(pred[r] - exact[r]) / exact[r];
+      errs.push_back(e);
+      bin_err[bin_of(m)] += e;
+      bin_err2[bin_of(m)] += e * e;
+      bin_cnt[bin_of(m)] += 1;
+    }
+  }
+  int n_bins_fb = 0;
+  std::vector<unsigned char> bin_fb(nbins, 0);
+  for (int b = 0; b < nbins; ++b) {
+    double e = 1e30;
+    if (bin_cnt[b] >= 16) {
+      const double n = bin_cnt[b], mu = bin_err[b] / n;
+      const double var = std::max(0.0, bin_err2[b] / n - mu * mu);
+      e = mu + 2.0 * std::sqrt(var / n);
+    }
+    if (e > so.tol) {
+      bin_fb[b] = 1;
+      ++n_bins_fb;
+    }
+  }
+  t0 = now_ms();
+  std::fill(mask.begin(), mask.end(), 0);
+  int n_fb = 0;
+  for (int m : pos)
+    if (!role[m] && bin_fb[bin_of(m)]) {
+      mask[m] = 1;
+      role[m] = 3;
+      ++n_fb;
+    }
+  std::vector<double> fb(rows_all, 0.0);
+  if (n_fb && (rc = exact_at(mask, fb))) {
+    cleanup();
+    return rc;
+  }
+  const double ms_fallback = now_ms() - t0;
+  for (int m = 0; m < nm; ++m)
+    for (int t = 0; t < nT; ++t) {
+      const size_t r = (size_t)t * nm + m;
+      double v;
+      unsigned char ex = 1;
+      if (!(om[m] > 0.0)) {
+        v = 0.0;
+      } else if (role[m] == 1 || role[m] == 2) {
+        v = exact[r];
+      } else if (role[m] == 3) {
+        v = fb[r];
+      } else {
+        v = pred[r];
+        ex = 0;
+      }
+      if (rates) rates[r] = v;
+      if (used_exact) used_exact[r] = ex;
+    }
+  if (rep) {
+    std::memset(rep, 0, sizeof(*rep));
+    rep->n_modes = (int)pos.size();
+    rep->n_train = n_train;
+    rep->n_holdout = n_hold;
+    rep->n_fallback_modes = n_fb;
+    rep->n_bins = nbins;
+    rep->n_bins_fallback = n_bins_fb;
+    rep->final_loss = final_loss;
+    std::sort(errs.begin(), errs.end());
+    if (!errs.empty()) {
+      rep->holdout_median_rel_err = errs[errs.size() / 2];
+      rep->holdout_p90_rel_err = errs[(size_t)(0.9 * (errs.size() - 1))];
+      rep->holdout_max_rel_err = errs.back();
+    }
+    rep->ms_exact = ms_exact;
+    rep->ms_features = ms_features;
+    rep->ms_train = ms_train;
+    rep->ms_predict = ms_predict;
+    rep->ms_fallback = ms_fallback;
+    rep->ms_total = now_ms() - t_start;
+  }
+  cleanup();
+#undef SW_TRY
   return FP_OK;
 }

@@ -16,34 +16,11 @@ from conftest import oracle_modes
 pytestmark = pytest.mark.gpu
 
 
-class SurOpts(ctypes.Structure):
-    _fields_ = [("train_frac", ctypes.c_double), ("holdout_frac", ctypes.c_double), ("tol", ctypes.c_double),
-                ("seed", ctypes.c_ulonglong), ("epochs", ctypes.c_int), ("batch", ctypes.c_int),
-                ("lr", ctypes.c_double), ("precision", ctypes.c_int)]
-
-
-class SurReport(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_int) for n in ("n_modes", "n_train", "n_holdout", "n_fallback_modes", "n_bins",
-                                            "n_bins_fallback")] + \
-               [(n, ctypes.c_double) for n in ("final_loss", "holdout_median_rel_err", "holdout_p90_rel_err",
-                                               "holdout_max_rel_err", "ms_exact", "ms_features", "ms_train",
-                                               "ms_predict", "ms_fallback", "ms_total")]
-
-
 @pytest.fixture(scope="module")
 def lib():
+    """The binding; its load() declares every argument type (the tests use its structures)."""
     from paper_2104_04895_gb300 import binding
-    L = binding.load()
-    dp = ctypes.POINTER(ctypes.c_double)
-    fp_ = ctypes.POINTER(ctypes.c_float)
-    L.fp_phase3.argtypes = [ctypes.c_void_p, ctypes.c_int, dp, ctypes.c_double, ctypes.c_void_p, dp, dp]
-    L.fp_mlp_params_size.argtypes = [ctypes.c_int]
-    L.fp_mlp_loss_grad.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, fp_, fp_, fp_, fp_, fp_]
-    L.fp_surrogate_default_opts.argtypes = [ctypes.POINTER(SurOpts)]
-    L.fp_surrogate_default_opts.restype = None
-    L.fp_surrogate_fit.argtypes = [ctypes.c_void_p, ctypes.c_int, dp, ctypes.c_double, ctypes.POINTER(SurOpts),
-                                   ctypes.POINTER(SurReport)]
-    L.fp_surrogate_rates.argtypes = [ctypes.c_void_p, dp, ctypes.POINTER(ctypes.c_ubyte)]
+    binding.load()
     return binding
 
 
@@ -116,9 +93,9 @@ def test_surrogate_fit_exact_entries_fallback_rule_and_gain(lib):
         t0 = time.perf_counter()
         exact, st = ctx.rates4(temps, cr.scalebroad, precision=lib.FP_PREC_MIXED)
         t_exact = time.perf_counter() - t0
-        so = SurOpts()
+        so = lib.fp_surrogate_opts()
         L.fp_surrogate_default_opts(ctypes.byref(so))
-        rep = SurReport()
+        rep = lib.fp_surrogate_report()
         t0 = time.perf_counter()
         assert L.fp_surrogate_fit(ctx.h, len(temps), _d(temps), cr.scalebroad, ctypes.byref(so),
                                   ctypes.byref(rep)) == 0
@@ -169,3 +146,38 @@ def test_phase4_matches_oracle_unit_vertex(lib, maker):
     assert np.max(np.abs(wp4[nz] - ref[nz]) / ref[nz]) <= 2e-5
     # the strided estimate is of the same size (it samples every other q')
     assert 0.5 < np.median(wp4_s[nz] / ref[nz]) < 2.0
+
+
+def test_surrogate_sweep_at_new_temperatures(lib):
+    """Learned rates at new temperatures: anchors at 300, 650 and 1000 K for every mode, and 16 output temperatures
+    (two batched evaluations for the exact path).  Exact entries are the exact rates bit for bit, the network's
+    entries are checked against exact rates of every mode, bins it keeps hold the 5 % rule, and the share of
+    entries evaluated exactly is reported."""
+    cr = synth.diamond_si((6, 6, 6))
+    anchors = [300.0, 650.0, 1000.0]
+    temps = list(np.linspace(300.0, 1000.0, 16))
+    with lib.Context.from_crystal(cr) as ctx:
+        ctx.modes(copy=False)
+        exact = np.concatenate([ctx.rates4(temps[i:i + 8], cr.scalebroad, precision=lib.FP_PREC_MIXED)[0]
+                                for i in range(0, 16, 8)])
+        rates, used, rep = ctx.surrogate_sweep(anchors, temps, cr.scalebroad)
+        with pytest.raises(lib.FourPhononError):
+            ctx.surrogate_sweep(anchors, [300.0] * 65, cr.scalebroad)
+        with pytest.raises(lib.FourPhononError):
+            ctx.surrogate_sweep([0.0], temps, cr.scalebroad)
+    ex = exact.reshape(16, -1)
+    ra = rates.reshape(16, -1)
+    us = used.reshape(16, -1).astype(bool)
+    pos = ex[0] > 0
+    assert np.array_equal(ra[us], ex[us]) and np.all(ra[:, ~pos] == 0.0)
+    pred = (~us) & (ex > 0)
+    share_exact = us[:, pos].mean()
+    if pred.any():
+        rel = np.abs(ra[pred] - ex[pred]) / ex[pred]
+        assert np.median(rel) <= 0.05
+        print(f"sweep: {pred.sum()} of {pos.sum() * 16} entries predicted (exact share {share_exact:.3f}); "
+              f"predicted rel err median {np.median(rel):.4f} p90 {np.quantile(rel, 0.9):.4f} max {rel.max():.4f}; "
+              f"held-out median {rep['holdout_median_rel_err']:.4f}; {rep['n_bins_fallback']}/{rep['n_bins']} bins exact")
+    else:
+        assert rep["n_bins_fallback"] == rep["n_bins"]
+    assert rep["n_train"] > 0 and rep["n_holdout"] > 0
