@@ -170,30 +170,32 @@ constexpr float kRelS = 1.0f / 524288.0f;         // 2^-19: prefilter margin per
 constexpr float kRelP = 1.0f / 4194304.0f;        // 2^-22: prefilter margin per unit of window*sigma
 constexpr float kAbsV = 1.0f / 1099511627776.0f;  // 2^-40: two-float velocity difference error per |v|_1
 
-// exp(-u) for the FP64 Gaussian, table-driven (P. T. P. Tang, ACM TOMS 15 (1989) 144-157): u = k h + r with
-// h = 1/64 and |r| <= h/2, exp(-u) = exp(-k h) exp(-r); exp(-k h) comes from a table of kExpTab entries
-// (0 <= u <= 4), exp(-r) from its Taylor polynomial of degree 5, whose truncation error (h/2)^6/6! < 4e-16 is
-// below two ulp. Larger u (only when the window exceeds 2) takes exp().
+// exp(-u) for the FP64 Gaussian, table-driven (P. T. P. Tang, ACM TOMS 15 (1989) 144-157), taking v = 64 u:
+// u = k h + r with h = 1/64, k = rint(v) and |r| <= h/2, exp(-u) = exp(-k h) exp(-r); exp(-k h) comes from a table
+// of kExpTab entries (0 <= u <= 4), exp(-r) from its Taylor polynomial of degree 5, whose truncation error
+// (h/2)^6/6! < 4e-16 is below two ulp. The polynomial runs in t = k - v = -64 r (exact: |t| <= 1/2 and k lies
+// within a factor 2 of v), with the coefficients 1/n! scaled by 64^-n, exact powers of two. Larger u (only when
+// the window exceeds 2) takes exp().
 constexpr double kSqrtPi = 1.7724538509055160273;  // sqrt(pi)
 constexpr int kExpTab = 264;
 constexpr double kExpH = 1.0 / 64.0;
-__device__ __forceinline__ double exp_neg(double u, const double* tab) {
-  if (!(u <= 4.0)) return exp(-u);
-  const int k = __double2int_rn(u * 64.0);
-  const double s = fma((double)k, kExpH, -u);  // -r, exact
-  double p = 1.0 / 120.0;
-  p = fma(p, s, 1.0 / 24.0);
-  p = fma(p, s, 1.0 / 6.0);
-  p = fma(p, s, 0.5);
-  p = fma(p, s, 1.0);
-  p = fma(p, s, 1.0);
+__device__ __forceinline__ double exp_neg64(double v, const double* tab) {
+  if (!(v <= 256.0)) return exp(-v * kExpH);
+  const int k = __double2int_rn(v);
+  const double t = (double)k - v;
+  double p = (1.0 / 120.0) / 1073741824.0;  // 64^-5 = 2^-30
+  p = fma(p, t, (1.0 / 24.0) / 16777216.0);  // 2^-24
+  p = fma(p, t, (1.0 / 6.0) / 262144.0);     // 2^-18
+  p = fma(p, t, 0.5 / 4096.0);               // 2^-12
+  p = fma(p, t, kExpH);
+  p = fma(p, t, 1.0);
   return tab[k] * p;
 }
 
 // Shared-memory carve shared by the kernel and the host-side size query.
 struct Carve {
   size_t E0, E1, E2, E3, Psi, T, Tw2, TwQ, ncx;                           // complex elements
-  size_t Om0, Om1, Om2, Om3, V1, V2, V3, Sig, W0, W1, W2, W3, Red, Wp, QD, ndbl, ExpT;  // doubles
+  size_t Om0, Om1, Om2, Om3, V1, V2, V3, Sig, SigW, W0, W1, W2, W3, Red, Wp, Wq, QD, ndbl, ExpT;  // doubles
   size_t Hq, Lq, H1, L1, H2, L2, H3, L3, VH1, VL1, VH2, VL2, VH3, VL3, Sigf, F0, F1, F2, F3, nflt;  // floats
   size_t KL, QI, EQ, nint;                                                        // ints
   size_t Mask;                                                                // bytes
@@ -213,8 +215,7 @@ __host__ __device__ constexpr int acc_slots(int nb) { return nb == 3 ? 3 : 2; }
 // f32: the FP32 path, which has no term queue, weight-product rows or exp table
 __host__ __device__ inline Carve make_carve(int nb, int J, int G, int nquart, int nT, int threads, bool f32) {
   Carve c;
-  const size_t nb2 = (size_t)nb * nb, nb3 = nb2 * nb, na = nb / 3;
-  const size_t rows = (size_t)J * nb2;
+  const size_t nb2 = (size_t)nb * nb, na = nb / 3;
   size_t o = 0;
   c.E0 = o; o += (size_t)J * nb;
   c.E1 = o; o += nb2;
@@ -235,12 +236,14 @@ __host__ __device__ inline Carve make_carve(int nb, int J, int G, int nquart, in
   c.V2 = d; d += 3 * nb;
   c.V3 = d; d += 3 * nb;
   c.Sig = d; d += 8 * nb2;
+  c.SigW = d; d += f32 ? 0 : 4 * nb2;  // FP64: (1/sigma) W3(j3) per sigma entry (one temperature)
   c.W0 = d; d += (size_t)nT * J;
   c.W1 = d; d += 2 * (size_t)nT * nb;
   c.W2 = d; d += 2 * (size_t)nT * nb;
   c.W3 = d; d += (size_t)nT * nb;
   c.Red = d; d += (size_t)threads * acc_slots(nb) * nT;
   c.Wp = d; d += f32 ? 0 : (size_t)threads * 4;  // FP64, one temperature: per-row weight products
+  c.Wq = d; d += f32 ? 0 : (size_t)J * nb * 3;    // FP64, one temperature: their (j0, q' branch) factors
   c.QD = d; d += f32 ? 0 : nwarps * kQCap;         // FP64: |W|^2 of queued terms
   c.ExpT = d; d += f32 ? 0 : kExpTab;
   c.ndbl = d;
@@ -486,7 +489,8 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
   double* sV1 = db + cv.V1;
   double* sV2 = db + cv.V2;
   double* sV3 = db + cv.V3;
-  double* sSig = db + cv.Sig;
+  double* sSig = db + cv.Sig;  // [4][NB][NB] (window * max(sigma, sigma_min), 8/sigma or -1 when delta := 1)
+  double* sSigW = db + cv.SigW;  // [4][NB][NB] (1/sigma) W3(j3), or sqrt(pi) W3(j3) when delta := 1
   double* sW0 = db + cv.W0;
   double* sW1 = db + cv.W1;
   double* sW2 = db + cv.W2;
@@ -494,6 +498,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
   double* sRed = db + cv.Red;
   double* sExpT = db + cv.ExpT;
   double* sWp = db + cv.Wp;  // [thread][4] (FP64, one temperature)
+  double* sWq = db + cv.Wq;  // [j0][q' branch][3] (FP64, one temperature)
   double* sQD = db + cv.QD;  // [warp][kQCap]
   float* fb = reinterpret_cast<float*>(db + cv.ndbl);
   float* sHq = fb + cv.Hq;
@@ -620,19 +625,24 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
       const int i1 = ordA ? ix : iy, i2 = ordA ? iy : ix;
       const int cls = (p == 0) ? 0 : (p == 2) ? 3 : ordA ? 1 : 2;
       const double d64 = dw_fp64(c, sOm0[jq], sOm1[ix], sOm2[iy], sOm3[j3]);
-      const double inv = sSig[2 * ent + 1];
+      const double iv8 = sSig[2 * ent + 1];  // 8 / sigma, or -1 when delta := 1
       // sqrt(pi) delta; the 1/sqrt(pi) is folded into the row weights (one temperature) or the multiplicity
-      double delta = kSqrtPi;
-      if (inv >= 0.0) {
-        const double xx = d64 * inv;
-        delta = exp_neg(xx * xx, sExpT) * inv;
-      }
       if constexpr (MAXT == 1) {
-        const double term = (W2 * delta) * sWp[4 * (jq * NB2 + ix * NB + iy) + cls] * sW3[j3];
+        double g = sSigW[ent];  // sqrt(pi) delta W3 = exp(-x^2) (1/sigma) W3
+        if (iv8 >= 0.0) {
+          const double x8 = d64 * iv8;
+          g *= exp_neg64(x8 * x8, sExpT);
+        }
+        const double term = (W2 * g) * sWp[4 * (jq * NB2 + ix * NB + iy) + cls];
 #pragma unroll
         for (int sl = 0; sl < S; ++sl)
           if (sl == slot) acc[sl][0] += term;
       } else {
+        double delta = kSqrtPi;
+        if (iv8 >= 0.0) {
+          const double x8 = d64 * iv8;
+          delta = exp_neg64(x8 * x8, sExpT) * (0.125 * iv8);
+        }
         const double base = (p == 2 ? kInvSqrtPi / 6.0 : 0.5 * kInvSqrtPi) * W2 * delta;
         const double* wq1 = ordA ? sW1 : sW2;
         const double* wq2 = ordA ? sW2 : sW1;
@@ -689,15 +699,26 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
         sTwQ[Q] = ld_tw<R>(a, e);
       }
       __syncthreads();
+      if constexpr (kF64 && MAXT == 1) {
+        // the (j0, q' branch) factors of the row weight products below: c_p (1/(n0 w0)) times the q' leg's
+        // (1+n)/w or n/w, with the 1/sqrt(pi) of the Gaussian; read after the barrier that ends the Psi prologue
+        for (int o = tid; o < J * NB; o += nthr) {
+          const double f0 = sW0[o / NB], a1 = sW1[2 * (o % NB)], b1 = sW1[2 * (o % NB) + 1];
+          sWq[3 * o] = (0.5 * kInvSqrtPi) * f0 * a1;
+          sWq[3 * o + 1] = (0.5 * kInvSqrtPi) * f0 * b1;
+          sWq[3 * o + 2] = (kInvSqrtPi / 6.0) * f0 * b1;
+        }
+      }
       // Psi[jj][j1][grp][gt]: one thread per (jj, j1, grp) and block of kGtb of the nine (gamma, theta); the
-      // nine products e0(alpha) e1(beta) of each quartet are formed once per block
+      // nine products e0(alpha) e1(beta) of each quartet are formed once per block. Tasks are numbered group-major,
+      // so the lanes of a warp mostly share one group: the same quartets, and the same trip count
       constexpr int kGtb = 3;
       const int npsi = unit ? 0 : J * NB * G * (9 / kGtb);
       for (int o = tid; o < npsi; o += nthr) {
         const int gb = o % (9 / kGtb);
-        const int t9 = o / (9 / kGtb);
-        const int grp = t9 % G;
-        const int jr = t9 / G;  // jj * NB + j1
+        const int jr = (o / (9 / kGtb)) % (J * NB);  // jj * NB + j1
+        const int grp = o / ((9 / kGtb) * J * NB);
+        const int t9 = jr * G + grp;
         const int j1 = jr % NB, jj = jr / NB;
         C sum[kGtb];
 #pragma unroll
@@ -826,6 +847,13 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
           } else {
             sigma_entry(a, vl, (double)sgn, sV3 + 3 * j3, sSig + 2 * o);
             sigma_f_from_exact(sSig + 2 * o, sSigPM + o, sSigI + o);
+            if constexpr (kF64) {
+              // the FP64 Gaussian takes (8 / sigma)^2 dw^2 = 64 x^2 and, with one temperature, the product
+              // (1/sigma) W3(j3) of two of its factors
+              const double inv = sSig[2 * o + 1];
+              if (MAXT == 1) sSigW[o] = (inv >= 0.0 ? inv : kSqrtPi) * sW3[j3];
+              sSig[2 * o + 1] = inv >= 0.0 ? 8.0 * inv : -1.0;
+            }
           }
         }
         if constexpr (kDF) {
@@ -837,17 +865,32 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
             const int ka = rc / 3, ga = rc % 3;
             const float4* psi_row = reinterpret_cast<const float4*>(sPsi) + (size_t)(rjj * NB + rj1) * G * 9 + ga * 3;
             const float4* twd = reinterpret_cast<const float4*>(sTw2);
+            // one pass over the groups of atom ka with every l (see the FP64 form below)
+            float4 cur[3] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
+                             make_float4(0.f, 0.f, 0.f, 0.f)};
+            int la = 0, seg_end = sKLs[ka * NA + 1];
+            auto put = [&]() {
 #pragma unroll
-            for (int la = 0; la < NA; ++la) {
-              const int kl = ka * NA + la;
-              for (int gi = sKLs[kl]; gi < sKLs[kl + 1]; ++gi) {
-                const int grp = sKLg[gi];
-                const float4 tw = twd[grp];
-                const float4* ps = psi_row + grp * 9;
+              for (int l = 0; l < NA; ++l)
+                if (l == la)
 #pragma unroll
-                for (int th = 0; th < 3; ++th) cdf_mac(Ad[3 * la + th], tw, ps[th]);
+                  for (int th = 0; th < 3; ++th) Ad[3 * l + th] = cur[th];
+#pragma unroll
+              for (int th = 0; th < 3; ++th) cur[th] = make_float4(0.f, 0.f, 0.f, 0.f);
+            };
+            const int g_end = sKLs[ka * NA + NA];
+            for (int gi = sKLs[ka * NA]; gi < g_end; ++gi) {
+              while (gi >= seg_end) {
+                put();
+                seg_end = sKLs[ka * NA + (++la) + 1];
               }
+              const int grp = sKLg[gi];
+              const float4 tw = twd[grp];
+              const float4* ps = psi_row + grp * 9;
+#pragma unroll
+              for (int th = 0; th < 3; ++th) cdf_mac(cur[th], tw, ps[th]);
             }
+            put();
             const float4* e3d = reinterpret_cast<const float4*>(sE3);
             float4* trow = reinterpret_cast<float4*>(sT + (size_t)(rjj * NB + rj1) * (NB2 + 1) + rc * NB);
 #pragma unroll
@@ -865,17 +908,34 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
           for (int d = 0; d < NB; ++d) Arow[d] = cmk<R>(0, 0);
           const int ka = rc / 3, ga = rc % 3;
           const C* psi_row = sPsi + (size_t)(rjj * NB + rj1) * G * 9 + ga * 3;
+          // one pass over the groups of atom ka with every l, which sit contiguously in l order: a lane's trip
+          // count is the number of groups of its atom, so lanes of different ka (in the same warp) run about the
+          // same count, where separate passes per l would each run the longest list of the warp. The running sum
+          // of the current l moves into Arow when l changes (register moves only)
+          C cur[3] = {cmk<R>(0, 0), cmk<R>(0, 0), cmk<R>(0, 0)};
+          int la = 0, seg_end = sKLs[ka * NA + 1];
+          auto put = [&]() {
 #pragma unroll
-          for (int la = 0; la < NA; ++la) {
-            const int kl = ka * NA + la;
-            for (int gi = sKLs[kl]; gi < sKLs[kl + 1]; ++gi) {
-              const int grp = sKLg[gi];
-              const C tw = sTw2[grp];
-              const C* ps = psi_row + grp * 9;
+            for (int l = 0; l < NA; ++l)
+              if (l == la)
 #pragma unroll
-              for (int th = 0; th < 3; ++th) cfma(Arow[3 * la + th], tw, ps[th]);
+                for (int th = 0; th < 3; ++th) Arow[3 * l + th] = cur[th];
+#pragma unroll
+            for (int th = 0; th < 3; ++th) cur[th] = cmk<R>(0, 0);
+          };
+          const int g_end = sKLs[ka * NA + NA];
+          for (int gi = sKLs[ka * NA]; gi < g_end; ++gi) {
+            while (gi >= seg_end) {
+              put();
+              seg_end = sKLs[ka * NA + (++la) + 1];
             }
+            const int grp = sKLg[gi];
+            const C tw = sTw2[grp];
+            const C* ps = psi_row + grp * 9;
+#pragma unroll
+            for (int th = 0; th < 3; ++th) cfma(cur[th], tw, ps[th]);
           }
+          put();
           if constexpr (TC) {
             // A operand row tid (real part in K 0..5, imaginary in K 6..11), split into tf32 hi + lo
             unsigned char* Ah = tcbuf + (size_t)(tid >> 7) * 2 * kTcTile;
@@ -976,13 +1036,13 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
             // the four distinct products c_p (1/(n0 w0)) x leg weights of this row, per candidate class
             // (++ both orderings, +- ordering A, +- ordering B, -- both orderings), read by any lane
             if (row_ok) {
-              const double f0 = sW0[jq0], a1 = sW1[2 * x], b1 = sW1[2 * x + 1], a2 = sW2[2 * y], b2 = sW2[2 * y + 1];
+              const double* fq = sWq + 3 * (jq0 * NB + x);
+              const double a2 = sW2[2 * y], b2 = sW2[2 * y + 1];
               double* wp = sWp + 4 * tid;
-              // with the 1/sqrt(pi) of the Gaussian
-              wp[0] = 0.5 * kInvSqrtPi * f0 * (a1 * a2);
-              wp[1] = 0.5 * kInvSqrtPi * f0 * (a1 * b2);
-              wp[2] = 0.5 * kInvSqrtPi * f0 * (a2 * b1);
-              wp[3] = (kInvSqrtPi / 6.0) * f0 * (b1 * b2);
+              wp[0] = fq[0] * a2;
+              wp[1] = fq[0] * b2;
+              wp[2] = fq[1] * a2;
+              wp[3] = fq[2] * b2;
             }
           }
           const float2* PA0 = sSigPM + 0 * NB2 + y * NB;
