@@ -63,7 +63,7 @@ def parse():
                    help="learned rates at new temperatures (36 temperatures, 3 anchors) instead of the bench line")
     p.add_argument("--configs", action="store_true",
                    help="per-workload study: time and oracle error of both precisions on workloads 1-5")
-    p.add_argument("--budget-s", type=float, default=300.0,
+    p.add_argument("--budget-s", type=float, default=240.0,
                    help="per-workload records: a precision whose full rate set is estimated above this many seconds "
                         "is timed on strided q-slices and extrapolated")
     p.add_argument("--no-configs", action="store_true",
