@@ -630,9 +630,15 @@ def measure_workload(binding, wl, budget_slice_s=10.0, full_max_s=300.0, oracle_
             _, st = ctx.rates4(cr.temps, cr.scalebroad, precision=prec, mode_mask=probe, no_graph=1)
             t_rep = st["ms"] * 1e-3 * nb * 3.0 * N * N * nb ** 3 / st["candidates_executed"]
             est = t_rep * full_exec / (nb * 3.0 * N * N * nb ** 3)
+            limit = df_full_max_s if (name == "double_float" and df_full_max_s is not None) else full_max_s
+            if 0.5 * limit < est < 2.0 * limit:
+                # near the limit: one q is not representative (accepted counts vary over the grid); 16 spread q
+                _, st = ctx.rates4(cr.temps, cr.scalebroad, precision=prec,
+                                   mode_mask=_slice_mask(cr, max(1, N // 16), 1), no_graph=1)
+                t_rep = st["ms"] * 1e-3 * nb * 3.0 * N * N * nb ** 3 / st["candidates_executed"]
+                est = t_rep * full_exec / (nb * 3.0 * N * N * nb ** 3)
             smask = np.zeros(N * nb, np.uint8)
             smask[sample] = 1
-            limit = df_full_max_s if (name == "double_float" and df_full_max_s is not None) else full_max_s
             if est <= limit:
                 out, st = ctx.rates4(cr.temps, cr.scalebroad, precision=prec)
                 secs = st["ms"] * 1e-3
