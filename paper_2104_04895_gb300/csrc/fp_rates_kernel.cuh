@@ -281,9 +281,11 @@ __host__ __device__ inline Carve make_carve(int nb, int J, int G, int nquart, in
 // out = (window * max(sigma, sigma_min), 1/sigma or -1 when delta := 1).
 __device__ __noinline__ void sigma_entry(const RatesArgs& a, const double* vl, double s, const double* v3,
                                          double* out) {
-  double dx = __dsub_rn(s * vl[0], v3[0]);
-  double dy = __dsub_rn(s * vl[1], v3[1]);
-  double dz = __dsub_rn(s * vl[2], v3[2]);
+  // s * vl with s = +1 or -1 is a sign flip: an integer operation rather than an FP64 multiply, same value
+  const unsigned long long flip = s < 0.0 ? 0x8000000000000000ULL : 0ULL;
+  double dx = __dsub_rn(__longlong_as_double(__double_as_longlong(vl[0]) ^ flip), v3[0]);
+  double dy = __dsub_rn(__longlong_as_double(__double_as_longlong(vl[1]) ^ flip), v3[1]);
+  double dz = __dsub_rn(__longlong_as_double(__double_as_longlong(vl[2]) ^ flip), v3[2]);
   double sigma;
   if (a.dq_mode == 0) {
     double s2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
