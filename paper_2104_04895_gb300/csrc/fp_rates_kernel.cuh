@@ -36,6 +36,7 @@
 #pragma once
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "fp_internal.cuh"
 #include "fp_tc.cuh"
@@ -154,6 +155,42 @@ __device__ __forceinline__ double cdf_abs2(float4 w) {
   return (double)s + (double)__fadd_rn(t, __fadd_rn(pe, qe));
 }
 
+// Double-float reals (float2: x high, y low) for the accepted-term evaluation of FP_PREC_DOUBLE_FLOAT with one
+// temperature: the frequency difference, the Gaussian and the products run on the FP32 pipes at about 2^-47
+// relative error per operation.
+__device__ __forceinline__ float2 df_make(double v) {
+  const float h = __double2float_rn(v);
+  return make_float2(h, __double2float_rn(v - (double)h));
+}
+// (h, l) renormalised, |h| >= |l| (fast two-sum)
+__device__ __forceinline__ float2 df_fast(float h, float l) {
+  const float s = __fadd_rn(h, l);
+  return make_float2(s, __fsub_rn(l, __fsub_rn(s, h)));
+}
+// a b: the high product exact through its fma residual, the cross terms in FP32, al bl dropped
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  const float e = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, __fmaf_rn(a.x, b.x, -p)));
+  return df_fast(p, e);
+}
+// a + b: two-sum of the high parts, low parts in FP32, renormalised
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float bb = __fsub_rn(s, a.x);
+  const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+  return df_fast(s, __fadd_rn(e, __fadd_rn(a.y, b.y)));
+}
+// |w|^2 of a double-float complex (re.h, re.l, im.h, im.l), as a double-float
+__device__ __forceinline__ float2 cdf_abs2_df(float4 w) {
+  const float ph = __fmul_rn(w.x, w.x), qh = __fmul_rn(w.z, w.z);
+  const float pe = __fmaf_rn(2.0f * w.x, w.y, __fmaf_rn(w.x, w.x, -ph));
+  const float qe = __fmaf_rn(2.0f * w.z, w.w, __fmaf_rn(w.z, w.z, -qh));
+  const float s = __fadd_rn(ph, qh);
+  const float bb = __fsub_rn(s, ph);
+  const float t = __fadd_rn(__fsub_rn(ph, __fsub_rn(s, bb)), __fsub_rn(qh, bb));
+  return df_fast(s, __fadd_rn(t, __fadd_rn(pe, qe)));
+}
+
 __device__ __forceinline__ int wrapi(int x, int n) {
   int r = x % n;
   return r < 0 ? r + n : r;
@@ -190,6 +227,26 @@ __device__ __forceinline__ double exp_neg64(double v, const double* tab) {
   p = fma(p, t, kExpH);
   p = fma(p, t, 1.0);
   return tab[k] * p;
+}
+
+// exp(-v / 64) in double-float for the double-float path, by the method of exp_neg64: k = rint(v), t = k - v
+// (|t| <= 1/2, a double-float), exp(-v / 64) = tab[k] exp(t / 64) with the degree-5 Taylor polynomial in t. Its
+// two smallest coefficients run in FP32 (their contribution is below 1e-10 and known to 2^-24 of it), the rest
+// in double-float; tab holds exp(-k / 64) as double-floats. v beyond the table (a window above 2) takes exp().
+constexpr double kE3 = 1.0 / 1572864.0;  // 1 / (3! 64^3)
+constexpr float kE3h = (float)kE3;
+constexpr float kE3l = (float)(kE3 - (double)kE3h);
+__device__ __forceinline__ float2 df_exp_neg64(float2 v, const float2* tab) {
+  if (!(v.x <= 256.0f)) return df_make(exp(-((double)v.x + (double)v.y) * kExpH));
+  const float kf = rintf(v.x);
+  const int k = (int)kf;
+  const float2 t = df_add(make_float2(__fsub_rn(kf, v.x), 0.f), make_float2(-v.y, 0.f));  // k - v.x is exact
+  const float c45 = __fmaf_rn((float)(1.0 / 128849018880.0), t.x, (float)(1.0 / 402653184.0));  // 1/(5! 64^5), 1/(4! 64^4)
+  float2 p = df_add(df_mul(make_float2(c45, 0.f), t), make_float2(kE3h, kE3l));
+  p = df_add(df_mul(p, t), make_float2(1.0f / 8192.0f, 0.f));  // 1 / (2! 64^2)
+  p = df_add(df_mul(p, t), make_float2(1.0f / 64.0f, 0.f));
+  p = df_add(df_mul(p, t), make_float2(1.0f, 0.f));
+  return df_mul(tab[k], p);
 }
 
 // Shared-memory carve shared by the kernel and the host-side size query.
@@ -463,6 +520,9 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
   constexpr int NB2 = NB * NB, NA = NB / 3;
   constexpr bool kF64 = sizeof(R) == 8;
   constexpr bool kDF = DF;
+  // double-float path with one temperature: the accepted terms are evaluated in double-float on the FP32 pipes
+  constexpr bool kDFC = DF && MAXT == 1;
+  using QT = typename std::conditional<kDFC, float2, double>::type;  // |W|^2 of a queued term
   static_assert(!TC || (!kF64 && NB == 6), "the tensor-core T contraction is built for the mixed path, nb = 6");
   static_assert(!DF || kF64, "the double-float contraction belongs to the FP64 path");
   using C = Cx<R>;
@@ -501,7 +561,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
   double* sExpT = db + cv.ExpT;
   double* sWp = db + cv.Wp;  // [thread][4] (FP64, one temperature)
   double* sWq = db + cv.Wq;  // [j0][q' branch][3] (FP64, one temperature)
-  double* sQD = db + cv.QD;  // [warp][kQCap]
+  QT* sQD = reinterpret_cast<QT*>(db + cv.QD);  // [warp][kQCap]
   float* fb = reinterpret_cast<float*>(db + cv.ndbl);
   float* sHq = fb + cv.Hq;
   float* sLq = fb + cv.Lq;
@@ -561,7 +621,9 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
     tc::fence_after_sync();
     tmem_base = *s_tmem;
   }
-  if constexpr (kF64)
+  if constexpr (kDFC)
+    for (int o = tid; o < kExpTab; o += nthr) reinterpret_cast<float2*>(sExpT)[o] = df_make(exp(-(double)o * kExpH));
+  else if constexpr (kF64)
     for (int o = tid; o < kExpTab; o += nthr) sExpT[o] = exp(-(double)o * kExpH);
   for (int o = tid; o < NA * NA + 1; o += nthr) sKLs[o] = a.kl_start[o];
   for (int o = tid; o < G; o += nthr) sKLg[o] = a.kl_grp[o];
@@ -614,7 +676,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
       }
     // FP64 path: one queued term (|W|^2 and info = c | j3 << 3 | y << 7 | x << 11 | jj << 15): Gaussian and
     // Bose weights into the accumulator slot of its j0
-    auto consume = [&](const double W2, const int info) {
+    auto consume = [&](const QT W2, const int info) {
       const int c = info & 7, j3 = (info >> 3) & 15, iy = (info >> 7) & 15, ix = (info >> 11) & 15;
       const int jq = info >> 15;
       const int slot = jq - jj_lo;
@@ -626,36 +688,81 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
       const int s1 = (p == 2) ? 1 : 0, s2 = (p == 0) ? 0 : 1;
       const int i1 = ordA ? ix : iy, i2 = ordA ? iy : ix;
       const int cls = (p == 0) ? 0 : (p == 2) ? 3 : ordA ? 1 : 2;
-      const double d64 = dw_fp64(c, sOm0[jq], sOm1[ix], sOm2[iy], sOm3[j3]);
-      const double iv8 = sSig[2 * ent + 1];  // 8 / sigma, or -1 when delta := 1
-      // sqrt(pi) delta; the 1/sqrt(pi) is folded into the row weights (one temperature) or the multiplicity
-      if constexpr (MAXT == 1) {
-        double g = sSigW[ent];  // sqrt(pi) delta W3 = exp(-x^2) (1/sigma) W3
-        if (iv8 >= 0.0) {
-          const double x8 = d64 * iv8;
-          g *= exp_neg64(x8 * x8, sExpT);
+      if constexpr (kDFC) {
+        // double-float: dw from the two-float frequencies by error-free sums, 64 x^2 = (dw 8/sigma)^2, the
+        // Gaussian, and the products, on the FP32 pipes
+        const float fh = ordA ? sH1[ix] : sH2[iy], fl = ordA ? sL1[ix] : sL2[iy];
+        const float sh = ordA ? sH2[iy] : sH1[ix], sl2 = ordA ? sL2[iy] : sL1[ix];
+        const float sg1 = (p == 2) ? -1.f : 1.f, sg2 = (p == 0) ? 1.f : -1.f;
+        float t0, e1, e2, e3;
+        two_sum(sHq[jq], sg1 * fh, t0, e1);
+        two_sum(t0, sg2 * sh, t0, e2);
+        two_sum(t0, -sH3[j3], t0, e3);
+        const float lo = (((sLq[jq] + sg1 * fl) + sg2 * sl2) - sL3[j3]) + ((e1 + e2) + e3);
+        const float2 dw = df_add(make_float2(t0, 0.f), make_float2(lo, 0.f));
+        const float2 iv8 = reinterpret_cast<const float2*>(sSig)[2 * ent + 1];  // 8 / sigma, or (-1, 0)
+        float2 g = reinterpret_cast<const float2*>(sSigW)[ent];                  // (1/sigma) W3, or sqrt(pi) W3
+        if (iv8.x >= 0.f) {
+          const float2 x8 = df_mul(dw, iv8);
+          g = df_mul(g, df_exp_neg64(df_mul(x8, x8), reinterpret_cast<const float2*>(sExpT)));
         }
-        const double term = (W2 * g) * sWp[4 * (jq * NB2 + ix * NB + iy) + cls];
+        const float2 term =
+            df_mul(df_mul(W2, g), reinterpret_cast<const float2*>(sWp)[4 * (jq * NB2 + ix * NB + iy) + cls]);
+        // two-float running sum of the slot (all terms are positive), moved to the FP64 sum every few q''
 #pragma unroll
         for (int sl = 0; sl < S; ++sl)
-          if (sl == slot) acc[sl][0] += term;
+          if (sl == slot) {
+            float sm, er;
+            two_sum(acch[sl][0], term.x, sm, er);
+            const float2 n = df_fast(sm, __fadd_rn(er, __fadd_rn(accl[sl][0], term.y)));
+            acch[sl][0] = n.x;
+            accl[sl][0] = n.y;
+          }
       } else {
-        double delta = kSqrtPi;
-        if (iv8 >= 0.0) {
-          const double x8 = d64 * iv8;
-          delta = exp_neg64(x8 * x8, sExpT) * (0.125 * iv8);
-        }
-        const double base = (p == 2 ? kInvSqrtPi / 6.0 : 0.5 * kInvSqrtPi) * W2 * delta;
-        const double* wq1 = ordA ? sW1 : sW2;
-        const double* wq2 = ordA ? sW2 : sW1;
-#pragma unroll
-        for (int t = 0; t < MAXT; ++t) {
-          if (t >= nT) break;
-          const double term = base * sW0[t * J + jq] * wq1[2 * (t * NB + i1) + s1] *
-                              wq2[2 * (t * NB + i2) + s2] * sW3[t * NB + j3];
+        const double d64 = dw_fp64(c, sOm0[jq], sOm1[ix], sOm2[iy], sOm3[j3]);
+        const double iv8 = sSig[2 * ent + 1];  // 8 / sigma, or -1 when delta := 1
+        // sqrt(pi) delta; the 1/sqrt(pi) is folded into the row weights (one temperature) or the multiplicity
+        if constexpr (MAXT == 1) {
+          double g = sSigW[ent];  // sqrt(pi) delta W3 = exp(-x^2) (1/sigma) W3
+          if (iv8 >= 0.0) {
+            const double x8 = d64 * iv8;
+            g *= exp_neg64(x8 * x8, sExpT);
+          }
+          const double term = (W2 * g) * sWp[4 * (jq * NB2 + ix * NB + iy) + cls];
 #pragma unroll
           for (int sl = 0; sl < S; ++sl)
-            if (sl == slot) acc[sl][t] += term;
+            if (sl == slot) acc[sl][0] += term;
+        } else {
+          double delta = kSqrtPi;
+          if (iv8 >= 0.0) {
+            const double x8 = d64 * iv8;
+            delta = exp_neg64(x8 * x8, sExpT) * (0.125 * iv8);
+          }
+          const double base = (p == 2 ? kInvSqrtPi / 6.0 : 0.5 * kInvSqrtPi) * W2 * delta;
+          const double* wq1 = ordA ? sW1 : sW2;
+          const double* wq2 = ordA ? sW2 : sW1;
+#pragma unroll
+          for (int t = 0; t < MAXT; ++t) {
+            if (t >= nT) break;
+            const double term = base * sW0[t * J + jq] * wq1[2 * (t * NB + i1) + s1] *
+                                wq2[2 * (t * NB + i2) + s2] * sW3[t * NB + j3];
+#pragma unroll
+            for (int sl = 0; sl < S; ++sl)
+              if (sl == slot) acc[sl][t] += term;
+          }
+        }
+      }
+    };
+
+    // double-float path, one temperature: the slots' two-float running sums into the FP64 sums (every 64 q'' and
+    // at the end of each q', so that a running sum holds a bounded number of terms)
+    auto flush_df = [&]() {
+      if constexpr (kDFC) {
+#pragma unroll
+        for (int sl = 0; sl < S; ++sl) {
+          acc[sl][0] += (double)acch[sl][0] + (double)accl[sl][0];
+          acch[sl][0] = 0.f;
+          accl[sl][0] = 0.f;
         }
       }
     };
@@ -706,9 +813,18 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
         // (1+n)/w or n/w, with the 1/sqrt(pi) of the Gaussian; read after the barrier that ends the Psi prologue
         for (int o = tid; o < J * NB; o += nthr) {
           const double f0 = sW0[o / NB], a1 = sW1[2 * (o % NB)], b1 = sW1[2 * (o % NB) + 1];
-          sWq[3 * o] = (0.5 * kInvSqrtPi) * f0 * a1;
-          sWq[3 * o + 1] = (0.5 * kInvSqrtPi) * f0 * b1;
-          sWq[3 * o + 2] = (kInvSqrtPi / 6.0) * f0 * b1;
+          const double w0 = (0.5 * kInvSqrtPi) * f0 * a1, w1 = (0.5 * kInvSqrtPi) * f0 * b1;
+          const double w2 = (kInvSqrtPi / 6.0) * f0 * b1;
+          if constexpr (kDFC) {  // as double-floats in the same slots
+            float2* wf = reinterpret_cast<float2*>(sWq + 3 * o);
+            wf[0] = df_make(w0);
+            wf[1] = df_make(w1);
+            wf[2] = df_make(w2);
+          } else {
+            sWq[3 * o] = w0;
+            sWq[3 * o + 1] = w1;
+            sWq[3 * o + 2] = w2;
+          }
         }
       }
       // Psi[jj][j1][grp][gt]: one thread per (jj, j1, grp) and block of kGtb of the nine (gamma, theta); the
@@ -813,7 +929,11 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
           const int it = o / NB, j = o % NB;
           const size_t i2 = 3 * ((size_t)it * NM + (size_t)k2 * NB + j);
           const size_t i3 = 3 * ((size_t)it * NM + (size_t)k3 * NB + j);
-          if (kF64) {
+          if constexpr (kDFC) {  // the q'' leg weights as double-floats in the same slots
+            reinterpret_cast<float2*>(sW2)[2 * o] = df_make(a.wt[i2 + 1]);
+            reinterpret_cast<float2*>(sW2)[2 * o + 1] = df_make(a.wt[i2 + 2]);
+            sW3[o] = a.wt[i3 + 2];
+          } else if (kF64) {
             sW2[2 * o] = a.wt[i2 + 1];
             sW2[2 * o + 1] = a.wt[i2 + 2];
             sW3[o] = a.wt[i3 + 2];
@@ -853,8 +973,13 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
               // the FP64 Gaussian takes (8 / sigma)^2 dw^2 = 64 x^2 and, with one temperature, the product
               // (1/sigma) W3(j3) of two of its factors
               const double inv = sSig[2 * o + 1];
-              if (MAXT == 1) sSigW[o] = (inv >= 0.0 ? inv : kSqrtPi) * sW3[j3];
-              sSig[2 * o + 1] = inv >= 0.0 ? 8.0 * inv : -1.0;
+              if constexpr (kDFC) {  // as double-floats in the same slots
+                reinterpret_cast<float2*>(sSigW)[o] = df_make((inv >= 0.0 ? inv : kSqrtPi) * sW3[j3]);
+                reinterpret_cast<float2*>(sSig)[2 * o + 1] = inv >= 0.0 ? df_make(8.0 * inv) : make_float2(-1.f, 0.f);
+              } else {
+                if (MAXT == 1) sSigW[o] = (inv >= 0.0 ? inv : kSqrtPi) * sW3[j3];
+                sSig[2 * o + 1] = inv >= 0.0 ? 8.0 * inv : -1.0;
+              }
             }
           }
         }
@@ -1038,13 +1163,24 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
             // the four distinct products c_p (1/(n0 w0)) x leg weights of this row, per candidate class
             // (++ both orderings, +- ordering A, +- ordering B, -- both orderings), read by any lane
             if (row_ok) {
-              const double* fq = sWq + 3 * (jq0 * NB + x);
-              const double a2 = sW2[2 * y], b2 = sW2[2 * y + 1];
-              double* wp = sWp + 4 * tid;
-              wp[0] = fq[0] * a2;
-              wp[1] = fq[0] * b2;
-              wp[2] = fq[1] * a2;
-              wp[3] = fq[2] * b2;
+              if constexpr (kDFC) {
+                const float2* fq = reinterpret_cast<const float2*>(sWq + 3 * (jq0 * NB + x));
+                const float2 a2 = reinterpret_cast<const float2*>(sW2)[2 * y];
+                const float2 b2 = reinterpret_cast<const float2*>(sW2)[2 * y + 1];
+                float2* wp = reinterpret_cast<float2*>(sWp + 4 * tid);
+                wp[0] = df_mul(fq[0], a2);
+                wp[1] = df_mul(fq[0], b2);
+                wp[2] = df_mul(fq[1], a2);
+                wp[3] = df_mul(fq[2], b2);
+              } else {
+                const double* fq = sWq + 3 * (jq0 * NB + x);
+                const double a2 = sW2[2 * y], b2 = sW2[2 * y + 1];
+                double* wp = sWp + 4 * tid;
+                wp[0] = fq[0] * a2;
+                wp[1] = fq[0] * b2;
+                wp[2] = fq[1] * a2;
+                wp[3] = fq[2] * b2;
+              }
             }
           }
           const float2* PA0 = sSigPM + 0 * NB2 + y * NB;
@@ -1060,7 +1196,11 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
             if (lane < count) ent = (unsigned)sEQ[ebase + ((eh + lane) & (kEQCap - 1))];
             eh = (eh + count) & (kEQCap - 1);
             en -= count;
-            double W2 = 1.0;
+            QT W2;
+            if constexpr (kDFC)
+              W2 = make_float2(1.f, 0.f);
+            else
+              W2 = 1.0;
             if (ent && !unit) {
               ++nwf;
               const int ej3 = (ent >> 6) & 15, ey = (ent >> 10) & 15, ex = (ent >> 14) & 15, ejq = ent >> 18;
@@ -1070,7 +1210,10 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
                 float4 Wd = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                 for (int c = 0; c < NB; ++c) cdf_mac(Wd, e2[c], tbe[c * NB]);
-                W2 = cdf_abs2(Wd);
+                if constexpr (kDFC)
+                  W2 = cdf_abs2_df(Wd);
+                else
+                  W2 = cdf_abs2(Wd);
               } else {
                 const C* tbe = sT + (size_t)(ejq * NB + ex) * (NB2 + 1) + ej3;
                 const C* e2 = sE2 + ey * NB;
@@ -1144,6 +1287,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
             consume(sQD[qbase + sl], sQI[qbase + sl]);
           }
           __syncwarp();
+          if (((k2 - k2_first) & 63) == 63) flush_df();
         } else {
           // ---- phase 3 (FP32 path): window of the row (jj, x, y), W in registers where a candidate is accepted,
           // then Gaussian and Bose weights
@@ -1250,6 +1394,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
         }
         __syncthreads();
       }
+      flush_df();
     }
     // deterministic reduction. FP64: per-lane slot sums in shared memory, then for each j0 the lanes of the
     // warps that hold its rows, in lane order. FP32: per-row sums, then the rows of each j0 in order.
