@@ -252,7 +252,7 @@ __device__ __forceinline__ float2 df_exp_neg64(float2 v, const float2* tab) {
 // Shared-memory carve shared by the kernel and the host-side size query.
 struct Carve {
   size_t E0, E1, E2, E3, Psi, T, Tw2, TwQ, ncx;                           // complex elements
-  size_t Om0, Om1, Om2, Om3, V1, V2, V3, Sig, SigW, W0, W1, W2, W3, Red, Wp, Wq, QD, ndbl, ExpT;  // doubles
+  size_t Om0, Om1, Om2, Om3, V1, V2, V3, Sig, SigW, W0, W1, W2, W3, Red, Wp, Wq, WA, WB, QD, ndbl, ExpT;  // doubles
   size_t Hq, Lq, H1, L1, H2, L2, H3, L3, VH1, VL1, VH2, VL2, VH3, VL3, Sigf, F0, F1, F2, F3, nflt;  // floats
   size_t KL, QI, EQ, nint;                                                        // ints
   size_t Mask;                                                                // bytes
@@ -301,6 +301,10 @@ __host__ __device__ inline Carve make_carve(int nb, int J, int G, int nquart, in
   c.Red = d; d += (size_t)threads * acc_slots(nb) * nT;
   c.Wp = d; d += f32 ? 0 : (size_t)threads * 4;  // FP64, one temperature: per-row weight products
   c.Wq = d; d += f32 ? 0 : (size_t)J * nb * 3;    // FP64, one temperature: their (j0, q' branch) factors
+  // FP64, several temperatures: Bose-weight products of the q leg with the k1 leg [T][j0][k1 branch][2] and of the
+  // k2 leg with the k3 leg [T][k2 branch][k3 branch][2]
+  c.WA = d; d += (f32 || nT == 1) ? 0 : (size_t)nT * J * nb * 2;
+  c.WB = d; d += (f32 || nT == 1) ? 0 : (size_t)nT * nb * nb * 2;
   c.QD = d; d += f32 ? 0 : nwarps * kQCap;         // FP64: |W|^2 of queued terms
   c.ExpT = d; d += f32 ? 0 : kExpTab;
   c.ndbl = d;
@@ -561,6 +565,8 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
   double* sExpT = db + cv.ExpT;
   double* sWp = db + cv.Wp;  // [thread][4] (FP64, one temperature)
   double* sWq = db + cv.Wq;  // [j0][q' branch][3] (FP64, one temperature)
+  double* sWA = db + cv.WA;  // [T][j0][k1 branch][2] (FP64, several temperatures)
+  double* sWB = db + cv.WB;  // [T][k2 branch][k3 branch][2] (FP64, several temperatures)
   QT* sQD = reinterpret_cast<QT*>(db + cv.QD);  // [warp][kQCap]
   float* fb = reinterpret_cast<float*>(db + cv.ndbl);
   float* sHq = fb + cv.Hq;
@@ -686,7 +692,6 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
       const int ent = tab * NB2 + (ordA ? iy : ix) * NB + j3;
       // Bose selectors: leg q' takes (1+n)/w unless --, leg q'' takes (1+n)/w only for ++
       const int s1 = (p == 2) ? 1 : 0, s2 = (p == 0) ? 0 : 1;
-      const int i1 = ordA ? ix : iy, i2 = ordA ? iy : ix;
       const int cls = (p == 0) ? 0 : (p == 2) ? 3 : ordA ? 1 : 2;
       if constexpr (kDFC) {
         // double-float: dw from the two-float frequencies by error-free sums, 64 x^2 = (dw 8/sigma)^2, the
@@ -739,13 +744,14 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
             delta = exp_neg64(x8 * x8, sExpT) * (0.125 * iv8);
           }
           const double base = (p == 2 ? kInvSqrtPi / 6.0 : 0.5 * kInvSqrtPi) * W2 * delta;
-          const double* wq1 = ordA ? sW1 : sW2;
-          const double* wq2 = ordA ? sW2 : sW1;
+          // the k1 leg is q' in ordering A (selector s1) and q'' in ordering B (s2); the k2 leg the other one
+          const int sx = ordA ? s1 : s2, sy = ordA ? s2 : s1;
+          const double* wa = sWA + 2 * (jq * NB + ix) + sx;
+          const double* wb = sWB + 2 * (iy * NB + j3) + sy;
 #pragma unroll
           for (int t = 0; t < MAXT; ++t) {
             if (t >= nT) break;
-            const double term = base * sW0[t * J + jq] * wq1[2 * (t * NB + i1) + s1] *
-                                wq2[2 * (t * NB + i2) + s2] * sW3[t * NB + j3];
+            const double term = (base * wa[2 * t * J * NB]) * wb[2 * t * NB2];
 #pragma unroll
             for (int sl = 0; sl < S; ++sl)
               if (sl == slot) acc[sl][t] += term;
@@ -825,6 +831,15 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
             sWq[3 * o + 1] = w1;
             sWq[3 * o + 2] = w2;
           }
+        }
+      }
+      if constexpr (kF64 && MAXT > 1) {
+        // W0(T, j0) times the k1 leg's (1+n)/w and n/w, per temperature; read after the Psi prologue's barrier
+        for (int o = tid; o < nT * J * NB; o += nthr) {
+          const int t = o / (J * NB), jq = (o / NB) % J, xb = o % NB;
+          const double w0 = sW0[t * J + jq];
+          sWA[2 * o] = w0 * sW1[2 * (t * NB + xb)];
+          sWA[2 * o + 1] = w0 * sW1[2 * (t * NB + xb) + 1];
         }
       }
       // Psi[jj][j1][grp][gt]: one thread per (jj, j1, grp) and block of kGtb of the nine (gamma, theta); the
@@ -957,6 +972,15 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
         }
         __syncthreads();
         // ---- phase 2: sigma tables; A row and T row
+        if constexpr (kF64 && MAXT > 1) {
+          // the k2 leg's (1+n)/w and n/w times W3(T, k3 branch), per temperature (read in phase 3)
+          for (int o = tid; o < nT * NB2; o += nthr) {
+            const int t = o / NB2, yb = (o / NB) % NB, j3b = o % NB;
+            const double w3 = sW3[t * NB + j3b];
+            sWB[2 * o] = sW2[2 * (t * NB + yb)] * w3;
+            sWB[2 * o + 1] = sW2[2 * (t * NB + yb) + 1] * w3;
+          }
+        }
         // sigma tables [tab][u][j3]: tab 0: v(k2,u)-v3, 1: -v(k2,u)-v3, 2: v(k1,u)-v3, 3: -v(k1,u)-v3
         for (int o = tid; o < 4 * NB2; o += nthr) {
           const int tab = o / NB2, u = (o / NB) % NB, j3 = o % NB;
