@@ -141,3 +141,34 @@ def test_licoo2_10x10x6_full_size_three_temperatures(lib):
     errm = rel_err(mixed.reshape(3, -1)[:, modes], a)
     print(f"LiCoO2 10x10x6 full size, 3 T: mixed vs FP64 {errm:.2e}")
     assert errm <= RTOL_MIXED
+
+
+@pytest.mark.skipif(os.environ.get("FP_LONG_PARITY") != "1",
+                    reason="the oracle needs about 15 minutes per mode on 16 cores; set FP_LONG_PARITY=1")
+@pytest.mark.parametrize("wl", [4, 5])
+def test_fp64_against_the_oracle_on_the_multi_temperature_workloads(lib, wl):
+    """FP64 (and double-float) rates of LiCoO2 10x10x6 (3 T) and diamond 16^3 (8 T) at full size against the oracle
+    on the lowest-frequency non-degenerate mode, with the full partner sums of Eq. tao0."""
+    cr = synth.workload(wl)
+    w, e, v = oracle_modes(cr)
+    nb = cr.nb
+    flat = np.asarray(w).reshape(-1)
+
+    def nondegenerate(m):
+        q, j = divmod(m, nb)
+        others = np.delete(np.asarray(w)[q], j)
+        return flat[m] > 0 and np.min(np.abs(others - flat[m])) > 1e-6 * max(1.0, flat[m])
+
+    mode = min((m for m in range(flat.size) if nondegenerate(m)), key=lambda m: flat[m])
+    mask = np.zeros(flat.size, np.uint8)
+    mask[mode] = 1
+    with lib.Context.from_crystal(cr) as ctx:
+        ctx.set_modes(w, e, v)
+        r64, _ = ctx.rates4(cr.temps, cr.scalebroad, mode_mask=mask)
+        rdf, _ = ctx.rates4(cr.temps, cr.scalebroad, mode_mask=mask, precision=FP_PREC_DOUBLE_FLOAT)
+    nT = len(cr.temps)
+    ref, _ = oracle.rates4(cr, w, e, v, sel=[mode], nthreads=CORES)
+    err64 = rel_err(r64.reshape(nT, -1)[:, mode], ref[:, 0])
+    errdf = rel_err(rdf.reshape(nT, -1)[:, mode], ref[:, 0])
+    print(f"{cr.name}: mode {mode}, FP64 {err64:.2e}, double-float {errdf:.2e}")
+    assert err64 <= RTOL_FP64 and errdf <= RTOL_FP64
