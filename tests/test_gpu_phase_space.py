@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 from paper_2104_04895_gb300 import bte, synth
-from paper_2104_04895_gb300.binding import FP_PREC_MIXED
+from paper_2104_04895_gb300.binding import FP_PREC_DOUBLE_FLOAT, FP_PREC_MIXED
 
 from conftest import oracle_modes
 
@@ -25,8 +25,8 @@ def lib():
 @pytest.mark.parametrize("maker", [lambda: synth.diamond_si((3, 3, 2)), lambda: synth.simple_cubic((4, 4, 4)),
                                    lambda: synth.licoo2((2, 2, 1))], ids=["diamond-3x3x2", "sc-4x4x4", "licoo2-2x2x1"])
 def test_phase_space_matches_the_oracle(lib, maker):
-    """Per-mode process counts exactly, P4 and WP4 to 1e-10 (FP64 path, stride 1, time reversal folded); the mixed
-    path keeps the counts and P4/WP4 within 2e-5."""
+    """Per-mode process counts exactly, P4 and WP4 to 1e-10 (FP64 and double-float paths, stride 1, time reversal
+    folded); the mixed path keeps the counts and P4/WP4 within 2e-5."""
     cr = maker()
     w, e, v = oracle_modes(cr)
     temps = [300.0, 900.0]
@@ -35,13 +35,14 @@ def test_phase_space_matches_the_oracle(lib, maker):
         ctx.set_modes(w, e, v)
         npr, p4, wp4 = ctx.phase_space4(temps, cr.scalebroad)
         nprm, p4m, wp4m = ctx.phase_space4(temps, cr.scalebroad, precision=FP_PREC_MIXED)
+        nprd, p4d, wp4d = ctx.phase_space4(temps, cr.scalebroad, precision=FP_PREC_DOUBLE_FLOAT)
         with pytest.raises(lib.FourPhononError):
             ctx.phase_space4(temps, cr.scalebroad, stride=0)
     ref_p4, _ = oracle.rates4(cr, w, e, v, temps=temps[:1], unit_vertex=2)
     ref_wp4, acc = oracle.rates4(cr, w, e, v, temps=temps, unit_vertex=True)
     counts = np.array([oracle.rates4(cr, w, e, v, temps=temps[:1], sel=[m], unit_vertex=True)[1].sum()
                        for m in range(N * nb)])
-    assert np.array_equal(npr, counts) and np.array_equal(nprm, counts)
+    assert np.array_equal(npr, counts) and np.array_equal(nprm, counts) and np.array_equal(nprd, counts)
     assert npr.sum() == acc.sum() > 0
     ref_p4 = ref_p4[0] / N ** 2
     ref_wp4 = ref_wp4 / N ** 2
@@ -49,6 +50,8 @@ def test_phase_space_matches_the_oracle(lib, maker):
     assert np.all(p4[~pos] == 0.0) and np.all(wp4[:, ~pos] == 0.0)
     assert np.max(np.abs(p4[pos] - ref_p4[pos]) / ref_p4[pos]) <= 1e-10
     assert np.max(np.abs(wp4[:, pos] - ref_wp4[:, pos]) / ref_wp4[:, pos]) <= 1e-10
+    assert np.max(np.abs(p4d[pos] - ref_p4[pos]) / ref_p4[pos]) <= 1e-10
+    assert np.max(np.abs(wp4d[:, pos] - ref_wp4[:, pos]) / ref_wp4[:, pos]) <= 1e-10
     assert np.max(np.abs(p4m[pos] - ref_p4[pos]) / ref_p4[pos]) <= 2e-5
     assert np.max(np.abs(wp4m[:, pos] - ref_wp4[:, pos]) / ref_wp4[:, pos]) <= 2e-5
 
