@@ -503,7 +503,7 @@ __host__ __device__ constexpr int min_blocks_for() { return sizeof(R) == 4 ? FP_
       const int ent_ = tab_ * NB2 + ((c_ < 3) ? y : x) * NB + j3;                                      \
       const double d64_ = dw_fp64(c_, w0, sOm1[x], sOm2[y], sOm3[j3]);                                 \
       double P64_;                                                                                     \
-      if (kF64 || !f32_sigma) {                                                                        \
+      if (!f32_sigma) {                                                                                \
         P64_ = sSig[2 * ent_];                                                                         \
       } else {                                                                                         \
         double ex_[2];                                                                                 \
@@ -601,7 +601,10 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
   const bool has_row = tid < rows;
   const int rjj = tid / NB2, rj1 = (tid / NB) % NB, rc = tid % NB;
   const size_t NM = (size_t)N * NB;
-  const bool f32_sigma = !kF64 && a.dq_mode == 0;
+  // isotropic |dq|: the window's sigma tables come from two-float velocities with a rigorous bound (exact
+  // decisions; FP64 entries only where the bound does not settle them), in both precisions
+  const bool f32_sigma = a.dq_mode == 0;
+  const double inv_sbdq = kF64 ? 1.0 / (a.sb * a.dq) : 0.0;  // FP64 path: 1/sigma = inv_sbdq / |dv|
   constexpr int S = acc_slots(NB);
   const int lane = tid & 31;
   const int qbase = (tid >> 5) * kQCap;
@@ -933,7 +936,7 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
         for (int o = tid; o < 3 * NB; o += nthr) {
           sV2[o] = a.vel[(size_t)k2 * NB * 3 + o];
           sV3[o] = a.vel[(size_t)k3 * NB * 3 + o];
-          if (!kF64) {
+          if (f32_sigma) {
             sVH2[o] = a.velh[(size_t)k2 * NB * 3 + o];
             sVL2[o] = a.vell[(size_t)k2 * NB * 3 + o];
             sVH3[o] = a.velh[(size_t)k3 * NB * 3 + o];
@@ -990,6 +993,26 @@ __global__ void __launch_bounds__(max_threads_for(NB), TC ? 2 : min_blocks_for<R
             const float* vlh = (tab < 2 ? sVH2 : sVH1) + 3 * u;
             const float* vll = (tab < 2 ? sVL2 : sVL1) + 3 * u;
             sigma_entry_f32(a, vlh, vll, sgn, sVH3 + 3 * j3, sVL3 + 3 * j3, vl, sV3 + 3 * j3, sSigPM + o, sSigI + o);
+            if constexpr (kF64) {
+              // the FP64 Gaussian's 8/sigma and, with one temperature, (1/sigma) W3(j3), from 1/sqrt(|dv|^2) (CUDA's
+              // rsqrt): the Gaussian's value needs 1/sigma to a few ulp, not the correctly rounded sigma that the
+              // window's exact decisions use; delta := 1 is the prefilter's exact decision (inverse -1)
+              double iv = -1.0;
+              if (sSigI[o] >= 0.f) {
+                const unsigned long long flip = sgn < 0.f ? 0x8000000000000000ULL : 0ULL;
+                const double dx = __dsub_rn(__longlong_as_double(__double_as_longlong(vl[0]) ^ flip), sV3[3 * j3]);
+                const double dy = __dsub_rn(__longlong_as_double(__double_as_longlong(vl[1]) ^ flip), sV3[3 * j3 + 1]);
+                const double dz = __dsub_rn(__longlong_as_double(__double_as_longlong(vl[2]) ^ flip), sV3[3 * j3 + 2]);
+                iv = rsqrt(fma(dx, dx, fma(dy, dy, dz * dz))) * inv_sbdq;
+              }
+              if constexpr (kDFC) {  // as double-floats in the same slots
+                reinterpret_cast<float2*>(sSigW)[o] = df_make((iv >= 0.0 ? iv : kSqrtPi) * sW3[j3]);
+                reinterpret_cast<float2*>(sSig)[2 * o + 1] = iv >= 0.0 ? df_make(8.0 * iv) : make_float2(-1.f, 0.f);
+              } else {
+                if (MAXT == 1) sSigW[o] = (iv >= 0.0 ? iv : kSqrtPi) * sW3[j3];
+                sSig[2 * o + 1] = iv >= 0.0 ? 8.0 * iv : -1.0;
+              }
+            }
           } else {
             sigma_entry(a, vl, (double)sgn, sV3 + 3 * j3, sSig + 2 * o);
             sigma_f_from_exact(sSig + 2 * o, sSigPM + o, sSigI + o);
