@@ -64,7 +64,7 @@ typedef struct {
 
 /* Options of fp_rates4.  Zero-initialised fields take the defaults of fp_default_opts(). */
 typedef struct {
-  int precision;                   /* FP_PREC_FP64 (default) or FP_PREC_MIXED */
+  int precision;                   /* FP_PREC_FP64 (default), FP_PREC_DOUBLE_FLOAT or FP_PREC_MIXED */
   double window;                   /* a term enters when |dw| <= window * max(sigma, sigma_min); default 2 */
   double sigma_min;                /* delta := 1 below this sigma (Sec. 2.4), rad/ps; default 1e-10 */
   int dq_mode;                     /* 0: |dq| = (|det B|/N)^(1/3); 1: per-axis sqrt(sum_a ((dv.b_a)/N_a)^2/3) */
