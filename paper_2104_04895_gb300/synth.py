@@ -18,6 +18,13 @@ constants are replaced by spring models of the same structures and masses):
   energy K (u_b - u_a)^4 / 4!, i.e. the quartet over sites (x1..x4) in {a, b}^4
   gets s1 s2 s3 s4 K with s = -1 on site a and +1 on site b.  Summing over any
   site index gives zero (the acoustic sum rule of Sec. 2.3, Eq. ASR).
+* Phi4, general form (`general=True`, parity tests only): per bond a 6^4 tensor over the
+  six displacement components of its two sites, entries N(0, 5 eV/A^4), averaged over
+  the 24 permutations of its four axes.  The quartet over sites (x1..x4) gets the
+  block of the tensor at those sites.  This keeps the transposition symmetry of
+  Eq. TS but, unlike the bond energy above, is not symmetric in the Cartesian indices
+  of one quartet alone (so a transposed Cartesian index changes the vertex), and it
+  does not obey the acoustic sum rule.
 * Seeds: numpy PCG64 with seed 2104_04895 + config index.
 
 The five workloads follow the published benchmark table of the method's build
@@ -159,6 +166,43 @@ def _fc4_from_bonds(bonds, tensors):
     return idx, val
 
 
+def _draw_pair_tensors(rng, n, scale=5.0):
+    """Per bond a 6^4 tensor over the (site, Cartesian) components of its two sites, N(0, scale) entrywise,
+    averaged over the 24 permutations of its axes."""
+    out = []
+    for _ in range(n):
+        T = rng.normal(0.0, scale, size=(6, 6, 6, 6))
+        out.append(sum(np.transpose(T, p) for p in itertools.permutations(range(4))) / 24.0)
+    return out
+
+
+def _fc4_from_pair_tensors(bonds, tensors):
+    """Quartet list from per-bond 6^4 tensors: the quartet over sites (x1..x4) in {a@0, b@R}^4 gets the 3^4 block
+    of the tensor at those sites, shifted so the first atom is in cell 0."""
+    acc = {}
+    for (a, b, R, _d), T in zip(bonds, tensors):
+        T8 = T.reshape(2, 3, 2, 3, 2, 3, 2, 3)
+        sites = [(a, (0, 0, 0), 0), (b, tuple(R), 1)]
+        for combo in itertools.product(sites, repeat=4):
+            c0 = np.asarray(combo[0][1])
+            atoms = tuple(s[0] for s in combo)
+            cells = tuple(tuple(int(v) for v in (np.asarray(s[1]) - c0)) for s in combo[1:])
+            key = (atoms, cells)
+            blk = T8[combo[0][2], :, combo[1][2], :, combo[2][2], :, combo[3][2], :]
+            acc[key] = acc.get(key, np.zeros((3, 3, 3, 3))) + blk
+    keys = sorted(acc)
+    idx = np.array([[*k[0], *k[1][0], *k[1][1], *k[1][2]] for k in keys], dtype=np.int32)
+    val = np.array([acc[k].reshape(81) for k in keys], dtype=np.float64)
+    return idx, val
+
+
+def _fc4(bonds, rng, general):
+    """Phi4 quartets of the bonds: the bond-energy form, or the general per-bond form (see the module notes)."""
+    if general:
+        return _fc4_from_pair_tensors(bonds, _draw_pair_tensors(rng, len(bonds)))
+    return _fc4_from_bonds(bonds, _draw_tensors(rng, len(bonds)))
+
+
 def _fc3_from_bonds(bonds, tensors):
     """Triplet list from third-order bond tensors: sites {a@0, b@R}^3 with the sign product of the bond's ends
     (-1 at a, +1 at b: the derivatives of K (u_b - u_a)^3 / 6), shifted so the first atom is in cell 0. Each
@@ -231,8 +275,9 @@ def _point_group_tensors(bond_vecs, tensors, ops):
 
 
 # --------------------------------------------------------------------------- structures
-def simple_cubic(grid=(4, 4, 4), seed_index=1, symmetric=False, temps=(300.0,), scalebroad=1.0):
-    """Simple cubic monatomic, a = 3.0 A, 28.0855 amu, central NN k1=1.0, NNN k2=0.5 eV/A^2."""
+def simple_cubic(grid=(4, 4, 4), seed_index=1, symmetric=False, temps=(300.0,), scalebroad=1.0, general=False):
+    """Simple cubic monatomic, a = 3.0 A, 28.0855 amu, central NN k1=1.0, NNN k2=0.5 eV/A^2.  general=True draws
+    the general per-bond Phi4 (module notes) instead of the bond-energy form."""
     a = 3.0
     lattice = np.eye(3) * a
     frac = np.zeros((1, 3))
@@ -242,18 +287,23 @@ def simple_cubic(grid=(4, 4, 4), seed_index=1, symmetric=False, temps=(300.0,), 
     i2, v2 = _fc2_springs(lattice, frac, shells)
     bonds = _bonds_unordered(lattice, frac, lambda i, j, d, r: abs(r - a) < 1e-6, a)
     rng = np.random.Generator(np.random.PCG64(SEED_BASE + seed_index))
-    K = _draw_tensors(rng, len(bonds))
     extra = {}
-    if symmetric:
-        K = _point_group_tensors([b[3] for b in bonds], K, _signed_perms())
-        extra["point_group"] = _signed_perms()
-    i4, v4 = _fc4_from_bonds(bonds, K)
+    if general:
+        if symmetric:
+            raise ValueError("the general Phi4 form is not point-group averaged")
+        i4, v4 = _fc4(bonds, rng, True)
+    else:
+        K = _draw_tensors(rng, len(bonds))
+        if symmetric:
+            K = _point_group_tensors([b[3] for b in bonds], K, _signed_perms())
+            extra["point_group"] = _signed_perms()
+        i4, v4 = _fc4_from_bonds(bonds, K)
     i3, v3 = _draw_fc3(bonds, seed_index)
-    return Crystal("simple-cubic" + ("-sym" if symmetric else ""), lattice, frac, mass, i2, v2, i4, v4,
-                   tuple(grid), tuple(temps), scalebroad, extra, i3, v3)
+    name = "simple-cubic" + ("-sym" if symmetric else "") + ("-gen" if general else "")
+    return Crystal(name, lattice, frac, mass, i2, v2, i4, v4, tuple(grid), tuple(temps), scalebroad, extra, i3, v3)
 
 
-def _fcc_two_atom(a, masses, name, grid, seed_index, symmetric, temps, scalebroad):
+def _fcc_two_atom(a, masses, name, grid, seed_index, symmetric, temps, scalebroad, general=False):
     lattice = 0.5 * a * np.array([[0.0, 1.0, 1.0], [1.0, 0.0, 1.0], [1.0, 1.0, 0.0]])
     frac = np.array([[0.0, 0.0, 0.0], [0.25, 0.25, 0.25]])
     mass = np.asarray(masses, dtype=np.float64)
@@ -264,33 +314,38 @@ def _fcc_two_atom(a, masses, name, grid, seed_index, symmetric, temps, scalebroa
     i2, v2 = _fc2_springs(lattice, frac, shells)
     bonds = _bonds_unordered(lattice, frac, lambda i, j, d, r: abs(r - r1) < 1e-6, r1)
     rng = np.random.Generator(np.random.PCG64(SEED_BASE + seed_index))
-    K = _draw_tensors(rng, len(bonds))
     extra = {}
-    if symmetric:
-        vecs = [b[3] for b in bonds]
-        ops = [g for g in _signed_perms()
-               if all(any(np.allclose(g @ d, e, atol=1e-8) for e in vecs) for d in vecs)]
-        K = _point_group_tensors(vecs, K, ops)
-        extra["point_group"] = ops
-    i4, v4 = _fc4_from_bonds(bonds, K)
+    if general:
+        if symmetric:
+            raise ValueError("the general Phi4 form is not point-group averaged")
+        i4, v4 = _fc4(bonds, rng, True)
+    else:
+        K = _draw_tensors(rng, len(bonds))
+        if symmetric:
+            vecs = [b[3] for b in bonds]
+            ops = [g for g in _signed_perms()
+                   if all(any(np.allclose(g @ d, e, atol=1e-8) for e in vecs) for d in vecs)]
+            K = _point_group_tensors(vecs, K, ops)
+            extra["point_group"] = ops
+        i4, v4 = _fc4_from_bonds(bonds, K)
     i3, v3 = _draw_fc3(bonds, seed_index)
-    return Crystal(name + ("-sym" if symmetric else ""), lattice, frac, mass, i2, v2, i4, v4,
-                   tuple(grid), tuple(temps), scalebroad, extra, i3, v3)
+    return Crystal(name + ("-sym" if symmetric else "") + ("-gen" if general else ""), lattice, frac, mass, i2, v2,
+                   i4, v4, tuple(grid), tuple(temps), scalebroad, extra, i3, v3)
 
 
-def diamond_si(grid=(8, 8, 8), seed_index=2, symmetric=False, temps=(300.0,), scalebroad=1.0):
+def diamond_si(grid=(8, 8, 8), seed_index=2, symmetric=False, temps=(300.0,), scalebroad=1.0, general=False):
     """Diamond Si-like: a = 5.43 A, 2 x 28.0855 amu, NN+NNN central and transverse springs."""
     return _fcc_two_atom(5.43, [28.0855, 28.0855], "diamond-si", grid, seed_index, symmetric,
-                         temps, scalebroad)
+                         temps, scalebroad, general)
 
 
-def zincblende_bas(grid=(12, 12, 12), seed_index=3, temps=(300.0,), scalebroad=1.0):
+def zincblende_bas(grid=(12, 12, 12), seed_index=3, temps=(300.0,), scalebroad=1.0, general=False):
     """Zincblende BAs-like: a = 4.78 A, B 10.81 and As 74.92 amu (large acoustic-optical gap)."""
     return _fcc_two_atom(4.78, [10.81, 74.92], "zincblende-bas", grid, seed_index, False,
-                         temps, scalebroad)
+                         temps, scalebroad, general)
 
 
-def licoo2(grid=(10, 10, 6), seed_index=4, temps=(300.0, 500.0, 700.0), scalebroad=1.0):
+def licoo2(grid=(10, 10, 6), seed_index=4, temps=(300.0, 500.0, 700.0), scalebroad=1.0, general=False):
     """Rhombohedral layered LiCoO2-like (R-3m), 4 atoms: Li, Co, O, O.
 
     a_hex = 2.82 A, c_hex = 14.05 A, O at +-(u,u,u) with u = 0.26.  Springs: bonds
@@ -330,10 +385,10 @@ def licoo2(grid=(10, 10, 6), seed_index=4, temps=(300.0, 500.0, 700.0), scalebro
     v2 = np.array([pairs[k].reshape(9) for k in keys], dtype=np.float64)
     bonds = _bonds_unordered(lattice, frac, cat_o, 1.2 * d_co)
     rng = np.random.Generator(np.random.PCG64(SEED_BASE + seed_index))
-    K = _draw_tensors(rng, len(bonds))
-    i4, v4 = _fc4_from_bonds(bonds, K)
+    i4, v4 = _fc4(bonds, rng, general)
     i3, v3 = _draw_fc3(bonds, seed_index)
-    return Crystal("licoo2", lattice, frac, mass, i2, v2, i4, v4, tuple(grid), tuple(temps), scalebroad, {}, i3, v3)
+    return Crystal("licoo2" + ("-gen" if general else ""), lattice, frac, mass, i2, v2, i4, v4, tuple(grid),
+                   tuple(temps), scalebroad, {}, i3, v3)
 
 
 TEMPS_SWEEP = tuple(float(t) for t in range(300, 1001, 100))

@@ -225,6 +225,13 @@ def test_umklapp_hand_worked_cases():
     d = idx((1, 1, 0), 2)                            # (1/2, 1/2, 0): four tied translates, (+1/2, +1/2, 0) wins
     assert oracle.umklapp(cr2, d, y, G, 1) == 1      # (1/2, 1/2, 0) + (1/2, 0, 0) - 0 - (0, 1/2, 0) = (1, 0, 0)
     assert oracle.umklapp(cr2, d, G, G, 1) == 0      # q''' = q
+    cr4 = synth.simple_cubic((4, 4, 4))  # 1/4, -1/4 and the tie 1/2 = -1/2 together: the tie rule decides
+    h, f, f3 = idx((2, 0, 0), 4), idx((1, 0, 0), 4), idx((3, 0, 0), 4)
+    G4 = 0
+    assert oracle.umklapp(cr4, h, f, G4, 0) == 1     # 1/2 + 1/4 + 0 - (-1/4) = 1 (with -1/2 it would be 0)
+    assert oracle.umklapp(cr4, f, f, G4, 0) == 0     # 1/4 + 1/4 + 0 - 1/2 = 0 (with -1/2 it would be 1)
+    assert oracle.umklapp(cr4, f3, f3, G4, 0) == 1   # -1/4 - 1/4 + 0 - 1/2 = -1
+    assert oracle.umklapp(cr4, h, f3, G4, 1) == 0    # 1/2 - 1/4 - 0 - 1/4 = 0
 
 
 def test_normal_and_umklapp_split_the_rate():

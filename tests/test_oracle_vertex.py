@@ -40,6 +40,10 @@ CASES = [
     lambda: synth.diamond_si((2, 1, 1)),
     lambda: synth.diamond_si((2, 2, 1)),
     lambda: synth.zincblende_bas((2, 2, 2)),
+    # the general Phi4 form: not symmetric in the Cartesian indices of one quartet, so the index order of Eq. V4
+    # (alpha with atom i, beta with j, gamma with k, theta with l) is tested
+    lambda: synth.diamond_si((2, 2, 1), general=True),
+    lambda: synth.zincblende_bas((2, 1, 1), general=True),
 ]
 
 
@@ -75,8 +79,9 @@ def test_supercell_sum_vanishes_off_momentum_shell(rng):
     assert np.abs(Vbad).max() < 1e-12 * np.abs(Vok).max()
 
 
-def test_vertex_leg_permutations(rng):
-    cr = synth.diamond_si((3, 3, 2))
+@pytest.mark.parametrize("general", [False, True], ids=["bond-phi4", "general-phi4"])
+def test_vertex_leg_permutations(rng, general):
+    cr = synth.diamond_si((3, 3, 2), general=general)
     w, e, v = oracle_modes(cr)
     N = cr.nq
     for trial in range(3):
