@@ -396,3 +396,64 @@ def test_double_float_tilings_temperatures_and_dq_mode(lib, tiles):
     out, st = run_gpu(lib, cr, w, e, v, precision=FP_PREC_DOUBLE_FLOAT, **tiles)
     compare(out.reshape(1, -1), ref, RTOL_FP64)
     assert np.array_equal(np.array(st["accepted"]), acc)
+
+
+GENERAL_CASES = [
+    ("sc-3x3x2-general", lambda: synth.simple_cubic((3, 3, 2), general=True)),
+    ("diamond-3x3x2-general", lambda: synth.diamond_si((3, 3, 2), general=True)),
+    ("bas-3x2x2-general", lambda: synth.zincblende_bas((3, 2, 2), general=True)),
+    ("licoo2-2x2x1-general", lambda: synth.licoo2((2, 2, 1), general=True)),
+]
+
+
+@pytest.mark.parametrize("name,maker", GENERAL_CASES, ids=[c[0] for c in GENERAL_CASES])
+def test_general_phi4_in_every_precision(lib, name, maker):
+    """Phi4 that is not symmetric in the Cartesian indices of one quartet (the general per-bond form, which keeps
+    Eq. TS): the order in which the library's assembly pairs the Cartesian indices with the four legs of Eq. V4 is
+    checked against the oracle's.  FP64 and double-float at 1e-10, mixed (and, for six branches, its tensor-core
+    contraction) within the mixed bound; accepted counts exact in all."""
+    from paper_2104_04895_gb300.binding import FP_PREC_DOUBLE_FLOAT
+    cr = maker()
+    w, e, v = oracle_modes(cr)
+    temps = [300.0, 700.0]
+    ref, acc = oracle.rates4(cr, w, e, v, temps=temps)
+    runs = [("fp64", dict(precision=FP_PREC_FP64), RTOL_FP64),
+            ("double-float", dict(precision=FP_PREC_DOUBLE_FLOAT), RTOL_FP64),
+            ("mixed", dict(precision=FP_PREC_MIXED), RTOL_MIXED)]
+    if cr.nb == 6:
+        runs.append(("mixed, tensor cores", dict(precision=FP_PREC_MIXED, tensor_cores=1), RTOL_MIXED))
+    for label, opts, rtol in runs:
+        out, st = run_gpu(lib, cr, w, e, v, temps=temps, **opts)
+        err = compare(out.reshape(len(temps), -1), ref, rtol)
+        assert np.array_equal(np.array(st["accepted"]), acc), label
+        print(f"{name} {label}: max rel err {err:.2e}")
+
+
+def test_empty_selections_and_temperature_limits(lib):
+    """Edge cases of the selection and the temperature batch: an all-zero mode mask and an empty q range write zeros
+    over the whole output (a NaN-filled device buffer) and count no candidates; eight temperatures (the batch
+    limit) match the oracle; nine are rejected, and the context stays usable."""
+    import torch
+    cr = synth.diamond_si((3, 2, 2))
+    w, e, v = oracle_modes(cr)
+    N, nb = cr.nq, cr.nb
+    with lib.Context.from_crystal(cr) as ctx:
+        ctx.set_modes(w, e, v)
+        out = torch.full((N * nb,), float("nan"), dtype=torch.float64, device="cuda")
+        for opts in (dict(mode_mask=np.zeros(N * nb, np.uint8)), dict(q_begin=4, q_end=4)):
+            for prec in (FP_PREC_FP64, FP_PREC_MIXED):
+                out.fill_(float("nan"))
+                st = ctx.rates4_device([300.0], out.data_ptr(), cr.scalebroad, precision=prec, **opts)
+                torch.cuda.synchronize()
+                assert torch.all(out == 0.0).item(), (opts.keys(), prec)
+                assert st["candidates"] == 0 and sum(st["accepted"]) == 0
+        temps = list(np.linspace(300.0, 1000.0, 8))
+        ref, acc = oracle.rates4(cr, w, e, v, temps=temps)
+        got, st = ctx.rates4(temps, cr.scalebroad)
+        compare(got.reshape(8, -1), ref, RTOL_FP64)
+        assert np.array_equal(np.array(st["accepted"]), acc)
+        with pytest.raises(lib.FourPhononError) as ei:
+            ctx.rates4(list(np.linspace(300.0, 1000.0, 9)), cr.scalebroad)
+        assert ei.value.code == lib.FP_EINVAL
+        again, _ = ctx.rates4(temps, cr.scalebroad)
+        assert np.array_equal(again, got)
