@@ -384,8 +384,13 @@ def main():
     # the other benchmark workloads, one record each (rank 0 of a single-GPU run)
     configs = None
     if ws == 1 and not args.no_configs and not args.grid:
-        configs = [measure_workload(binding, wl, full_max_s=args.budget_s, df_full_max_s=min(60.0, args.budget_s),
-                                    tensor_cores=False) for wl in (1, 3, 4, 5)]
+        configs = []
+        for wl in (1, 3, 4, 5):
+            try:
+                configs.append(measure_workload(binding, wl, full_max_s=args.budget_s,
+                                                df_full_max_s=min(60.0, args.budget_s), tensor_cores=False))
+            except Exception as exc:  # a failed record is reported in the line; it must not cost the main line
+                configs.append({"workload": synth.WORKLOAD_NAMES[wl], "error": f"{type(exc).__name__}: {exc}"})
 
     if rank == 0:
         base = None
