@@ -1,5 +1,5 @@
 // Four-phonon RTA rate kernel template (paper Sec. 2.2 Eqs. tao0, 4phgamma, V4; Sec. 2.4).
-// Instantiated per precision in fp_rates_f64.cu and fp_rates_f32.cu; host logic is in fp_rates.cu.
+// Instantiated per precision in fp_rates_f64.cu, fp_rates_df.cu and fp_rates_f32.cu; host logic is in fp_rates.cu.
 //
 // One function W serves all three processes.  With k3 = q + k1 + k2 (mod G) and e(-k) = conj e(k),
 //   W(q,j0; k1,j1; k2,j2; k3,j3) = sum_quartets sum_{abgt} Phi4/sqrt(M^4) e_a(q,j0) e_b(k1,j1) e_g(k2,j2)
@@ -28,11 +28,16 @@
 // identical to the FP64 evaluation.  delta = exp(-(dw/sigma)^2)/(sqrt(pi) sigma), or 1 when
 // sigma < sigma_min.
 //
-// Precision of the two instantiations:
+// Precision of the instantiations:
 //   double: vertex, sigma, dw, Gaussian (table-driven exp), Bose weights and sums in FP64.
+//   double with DF = true: as double, but the vertex assembly and both contractions run in double-float
+//           (pairs of floats, about 2^-48 per operation) on the FP32 pipes, and with one temperature so do the
+//           accepted terms (dw from two-float frequencies, Gaussian, Bose and row weights, running sums that
+//           move into FP64 sums at fixed points); window decisions and sums across lanes and items stay FP64.
 //   float:  vertex assembly and contraction in FP32; dw from two-float frequencies (error-free sums,
 //           |error| <= 2^-44 sum(w)); sigma from two-float velocities; Gaussian and Bose weights in FP32;
-//           compensated (two-float) per-thread sums, FP64 across threads and work items.
+//           compensated (two-float) per-thread sums, FP64 across threads and work items.  With TC = true the
+//           per-q'' contraction T runs on the tensor cores (fp_tc.cuh).
 #pragma once
 #include <cmath>
 #include <cstring>
