@@ -353,13 +353,18 @@ def main():
                   "value": cands_step * args.steps / (t_ms * 1e-3), "unit": "process-terms/s",
                   "s_per_rate_set": t_ms / args.steps * 1e-3, "tile": t_st["tile"], "kernel_ms": t_kms}
 
-    # three-phonon rates of the same workload (FP64, one launch after a warm-up launch), for context
+    # three-phonon rates of the same workload (FP64), for context: the mean device time of `steps` rate sets
+    # after `warmup`, each from CUDA events on the library's stream
     three = None
     if not args.no_other and cr.fc3_idx is not None:
-        ctx.rates3(cr.temps, cr.scalebroad, **part)
-        _, st3 = ctx.rates3(cr.temps, cr.scalebroad, **part)
-        s3 = max_over_ranks(st3["ms"], dist if ws > 1 else None, dev) * 1e-3
-        three = {"precision": "fp64", "s_per_rate_set": s3, "candidates": st3["candidates"],
+        for _ in range(args.warmup):
+            ctx.rates3(cr.temps, cr.scalebroad, **part)
+        ms3 = []
+        for _ in range(max(1, args.steps)):
+            _, st3 = ctx.rates3(cr.temps, cr.scalebroad, **part)
+            ms3.append(st3["ms"])
+        s3 = max_over_ranks(float(np.mean(ms3)), dist if ws > 1 else None, dev) * 1e-3
+        three = {"precision": "fp64", "s_per_rate_set": s3, "steps": len(ms3), "candidates": st3["candidates"],
                  "terms_per_s": st3["candidates"] / s3, "accepted": st3["accepted"][:2]}
 
     # end to end through the public API with host buffers
