@@ -2,6 +2,8 @@
 
   python -m paper_2104_04895_gb300 onlyharmonic --workload 2 --out run/     # phase space: Numprocess, P4, WP4
   python -m paper_2104_04895_gb300 rta --workload 2 --out run/              # RTA rates, normal and Umklapp parts
+  python -m paper_2104_04895_gb300 rta --workload 5 --out run/ --checkpoint ck/ --slices 16 --no-nu-split
+                                                                            # resumable: rerun after a stop
 
 The crystal is one of the seeded synthetic workloads (paper_2104_04895_gb300.synth); --fc4 FILE replaces its
 fourth-order force constants by those of a FORCE_CONSTANTS_4TH file (--fc3 likewise for the third order), and
@@ -17,7 +19,7 @@ import time
 
 import numpy as np
 
-from . import binding, bte, synth
+from . import binding, bte, resume, synth
 
 
 def parse(argv):
@@ -33,6 +35,10 @@ def parse(argv):
     p.add_argument("--write-fc4", default=None, help="write the crystal's fourth-order force constants here")
     p.add_argument("--write-fc3", default=None, help="write the crystal's third-order force constants here")
     p.add_argument("--no-nu-split", action="store_true", help="rta: skip the normal/Umklapp parts")
+    p.add_argument("--checkpoint", default=None,
+                   help="rta: run the rates in slices of whole pairs {q, -q} with one checkpoint file per finished "
+                        "slice in this directory; a rerun loads the finished slices (paper_2104_04895_gb300.resume)")
+    p.add_argument("--slices", type=int, default=8, help="rta with --checkpoint: number of slices")
     p.add_argument("--device", type=int, default=0)
     p.add_argument("--out", required=True)
     return p.parse_args(argv)
@@ -65,7 +71,11 @@ def main(argv=None) -> int:
             paths = bte.write_phase_space(a.out, w, temps, npr, p4, wp4)
             summary = {"processes": float(np.sum(npr))}
         else:
-            rates, st = ctx.rates4(temps, cr.scalebroad, precision=prec)
+            if a.checkpoint:
+                rates, st = resume.rates4_resumable(ctx, temps, cr.scalebroad, a.checkpoint, a.slices,
+                                                    precision=prec)
+            else:
+                rates, st = ctx.rates4(temps, cr.scalebroad, precision=prec)
             normal = umklapp = None
             if not a.no_nu_split:
                 nu, _ = ctx.rates4_nu(temps, cr.scalebroad, precision=prec)
