@@ -60,9 +60,11 @@ class fp_stats(ctypes.Structure):
 
 
 EXPORTS = ["fp_version", "fp_default_opts", "fp_init", "fp_set_stream", "fp_modes", "fp_set_modes", "fp_rates4",
-           "fp_rates4_channels", "fp_rates4_nu", "fp_set_fc3", "fp_rates3", "fp_kappa_rta", "fp_rates4_irreducible", "fp_star_table", "fp_rates4_device", "fp_rates4_noalloc", "fp_autotune", "fp_phase3", "fp_phase4", "fp_mlp_params_size",
-           "fp_mlp_loss_grad", "fp_surrogate_default_opts", "fp_surrogate_fit", "fp_surrogate_rates", "fp_free",
-           "fp_last_error", "fp_phase_space4", "fp_surrogate_sweep", "fp_write_fc4", "fp_read_fc4", "fp_write_fc3", "fp_read_fc3"]
+           "fp_rates4_channels", "fp_rates4_nu", "fp_set_fc3", "fp_rates3", "fp_kappa_rta", "fp_rates4_irreducible",
+           "fp_star_table", "fp_rates4_device", "fp_rates4_noalloc", "fp_autotune", "fp_phase3", "fp_phase4",
+           "fp_mlp_params_size", "fp_mlp_loss_grad", "fp_surrogate_default_opts", "fp_surrogate_fit",
+           "fp_surrogate_rates", "fp_free", "fp_last_error", "fp_phase_space4", "fp_surrogate_sweep", "fp_write_fc4",
+           "fp_read_fc4", "fp_write_fc3", "fp_read_fc3"]
 
 
 class fp_surrogate_opts(ctypes.Structure):
@@ -80,6 +82,7 @@ class fp_surrogate_report(ctypes.Structure):
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
+
 
 _LIB = None
 
