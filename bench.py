@@ -400,7 +400,9 @@ def main():
     if rank == 0:
         base = None
         rel_err = rel_err_other = None
-        if not args.no_cpu_baseline:
+        # the oracle baseline and the sampled error check run at N = 1 only: with several GPUs rank 0 holds only the
+        # rates of its own q-points
+        if not args.no_cpu_baseline and ws == 1:
             base, sel, ref = cpu_baseline(cr, args.cpu_sample_seconds, w, e, v)
             gpu = out.view(nT, N * nb).cpu().numpy()[:, sel]
             rel_err = float(np.max(np.abs(gpu - ref) / np.abs(ref)))
