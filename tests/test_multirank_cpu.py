@@ -154,3 +154,31 @@ def test_balanced_shard_beats_contiguous_ranges():
     contiguous = [list(range(*shard(12 ** 3, 8, r))) for r in range(8)]
     loads = [sum(c[q] for q in p) for p in contiguous]
     assert max(loads) / np.mean(loads) > 1.1
+
+
+def test_cost_estimate_adds_a_common_share():
+    """estimate_costs: each q-point's accepted terms from one screening pass (here a stand-in context), plus a part
+    that every q-point pays alike, set to the given share of the mean cost; the q' stride defaults to N / 32."""
+    from paper_2104_04895_gb300.sharding import estimate_costs
+
+    class Ctx:
+        N, nb = 64, 3
+
+        def __init__(self, counts):
+            self.counts, self.calls = counts, []
+
+        def phase_space4(self, temps, scalebroad, stride=1, precision=0):
+            self.calls.append((list(temps), scalebroad, stride))
+            return self.counts, None, None
+
+    rng = np.random.Generator(np.random.PCG64(3))
+    counts = rng.integers(0, 1000, size=Ctx.N * Ctx.nb).astype(float)
+    ctx = Ctx(counts)
+    c = estimate_costs(ctx, [300.0, 600.0], 1.0, fixed_share=0.4)
+    per_q = counts.reshape(Ctx.N, Ctx.nb).sum(axis=1)
+    fixed = c - per_q
+    assert np.allclose(fixed, fixed[0]) and fixed[0] > 0
+    assert abs(fixed[0] / c.mean() - 0.4) < 1e-12
+    assert ctx.calls == [([300.0], 1.0, 2)]        # one temperature, stride N / 32
+    zero = estimate_costs(Ctx(np.zeros(Ctx.N * Ctx.nb)), [300.0], 1.0)
+    assert np.all(zero == 1.0)                      # no counts: equal costs
