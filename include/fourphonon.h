@@ -119,8 +119,10 @@ void fp_default_opts(fp_rates_opts* opts);
 /*
  * Create a context on `device` and upload the crystal: lattice rows a1..a3 (A), natoms fractional
  * positions (natoms x 3, informational: phases use cell vectors, Eq. V4), masses (amu, > 0), the
- * Phi2 pair list and the Phi4 quartet list, and the q-grid (each N_a >= 1).  Indices must lie in
- * [0, natoms).  On success *out owns all device memory of the problem; free it with fp_free().
+ * Phi2 pair list and the Phi4 quartet list, and the q-grid (each N_a in [1, 64]).  natoms must lie in
+ * [1, 4]; the four- and three-phonon rate kernels are built for 1, 2 and 4 atoms (nb = 3, 6, 12), and
+ * the rate calls return FP_EINVAL for 3.  Indices must lie in [0, natoms).  On success *out owns all device
+ * memory of the problem; free it with fp_free().
  */
 int fp_init(fp_ctx** out, const double lattice[9], int natoms, const double* frac_pos, const double* mass,
             int n_fc2, const fp_fc2* fc2, int n_fc4, const fp_fc4* fc4, const int grid[3], int device);
