@@ -393,7 +393,8 @@ def main():
         for wl in (1, 3, 4, 5):
             try:
                 configs.append(measure_workload(binding, wl, full_max_s=args.budget_s,
-                                                df_full_max_s=min(60.0, args.budget_s), tensor_cores=False))
+                                                df_full_max_s=min(60.0, args.budget_s), tensor_cores=False,
+                                                oracle_check=not args.no_cpu_baseline))
             except Exception as exc:  # a failed record is reported in the line; it must not cost the main line
                 configs.append({"workload": synth.WORKLOAD_NAMES[wl], "error": f"{type(exc).__name__}: {exc}"})
 
@@ -606,7 +607,7 @@ def _slice_mask(cr, m, k):
 
 
 def measure_workload(binding, wl, budget_slice_s=10.0, full_max_s=300.0, oracle_max_s=150.0, df_full_max_s=None,
-                     tensor_cores=True):
+                     tensor_cores=True, oracle_check=True):
     """Seconds per full-grid rate set of workload `wl` in each precision, and errors on sampled modes.
 
     An FP64 or mixed rate set estimated (from a one-q probe) to stay under `full_max_s` is timed on the whole grid,
@@ -614,27 +615,25 @@ def measure_workload(binding, wl, budget_slice_s=10.0, full_max_s=300.0, oracle_
     `tensor_cores` is set and the mixed set ran in full.  Otherwise three strided q-slices (q = k mod m, all
     branches) of about `budget_slice_s` each are timed and scaled to the grid
     by the candidates the kernel screened (time reversal evaluates (N + self-conjugate points) / 2 points of a full
-    grid); the spread of the three gives the sampling uncertainty.  The GPU takes the oracle's modes, so the error
-    against the oracle on a ruled mode sample (lowest positive frequency and one seeded mode) is a strict one; the
-    oracle runs only where it finishes within `oracle_max_s` on the host cores."""
-    import oracle
-    import oracle.modes as om
+    grid); the spread of the three gives the sampling uncertainty.  The rates use the library's own modes
+    (fp_modes); with `oracle_check`, the oracle (the CPU-baseline leg of this record) recomputes a ruled mode sample
+    (lowest positive frequency and one seeded mode) from the same mode tables, so the error is a strict one; it runs
+    only where it finishes within `oracle_max_s` on the host cores."""
     cr = synth.workload(wl)
     N, nb, nT = cr.nq, cr.nb, len(cr.temps)
     cands = 3.0 * N ** 3 * nb ** 4
     full_exec = 3.0 * N * N * nb ** 3 * nb * (N + _self_conjugate(cr.grid)) / 2.0
-    w, e, v = om.modes(cr)
-    flat = w.reshape(-1)
-    pos = np.nonzero(flat > 0)[0]
-    rng = np.random.Generator(np.random.PCG64(77 + wl))
-    sample = [int(pos[np.argmin(flat[pos])]), int(rng.choice(pos))]
-    if N * nb > 5000:
-        sample = sample[:1]  # the oracle takes a minute or more per mode here
-    res = {"workload": synth.WORKLOAD_NAMES[wl], "candidates": cands, "temperatures": nT,
-           "sample_modes": sample}
     outs = {}
     with binding.Context.from_crystal(cr) as ctx:
-        ctx.set_modes(w, e, v)
+        w, e, v = ctx.modes()
+        flat = w.reshape(-1)
+        pos = np.nonzero(flat > 0)[0]
+        rng = np.random.Generator(np.random.PCG64(77 + wl))
+        sample = [int(pos[np.argmin(flat[pos])]), int(rng.choice(pos))]
+        if N * nb > 5000:
+            sample = sample[:1]  # the oracle takes a minute or more per mode here
+        res = {"workload": synth.WORKLOAD_NAMES[wl], "candidates": cands, "temperatures": nT,
+               "sample_modes": sample, "modes": "fp_modes (GPU)"}
         for name, prec in (("fp64", binding.FP_PREC_FP64), ("double_float", binding.FP_PREC_DOUBLE_FLOAT),
                            ("mixed", binding.FP_PREC_MIXED)):
             probe = np.zeros(N * nb, np.uint8)
@@ -683,7 +682,10 @@ def measure_workload(binding, wl, budget_slice_s=10.0, full_max_s=300.0, oracle_
     # oracle cost per mode on these host cores: about 3 N^2 nb^3 terms at 1.6e7 (6 / nb)^3 terms/s on 16 cores
     cores = os.cpu_count() or 1
     t_or = 3.0 * N ** 2 * nb ** 3 / (1.6e7 * (6.0 / nb) ** 3 * cores / 16.0)
-    if t_or * len(sample) <= oracle_max_s:
+    if not oracle_check:
+        res["oracle"] = {"skipped": "no CPU baseline in this run"}
+    elif t_or * len(sample) <= oracle_max_s:
+        import oracle
         t0 = time.perf_counter()
         ref, _ = oracle.rates4(cr, w, e, v, sel=sample, nthreads=cores)
         dt = time.perf_counter() - t0
