@@ -33,7 +33,7 @@ MLP = "tests/test_oracle_mlp.py"
 PINS = [DELTA, RATES + "::test_single_q_closed_form_in_si_units"]
 CLOSED = [RATES + "::test_single_q_closed_form_in_si_units", RATES + "::test_detailed_balance_on_shell"]
 BRUTE = [VERTEX]
-UMKLAPP = [RATES + "::test_umklapp_hand_worked_cases"]
+UMKLAPP = [RATES + "::test_umklapp_hand_worked_cases", RATES + "::test_umklapp_reading_on_a_sheared_cell"]
 
 # (name, text, replacement, pins): the first occurrence of the text is the one in oracle_rates4
 MUTANTS = [
@@ -105,6 +105,12 @@ C_MUTANTS = [
     ("umklapp-ties-to-the-largest-shift", "if (best < 0.0 || k2 < best * (1.0 - 1e-9)) {",
      "if (best < 0.0 || k2 <= best * (1.0 + 1e-9)) {", UMKLAPP),
     ("umklapp-sign-of-q'''", "- (g3[a] - n * m3[a]);", "+ (g3[a] - n * m3[a]);", UMKLAPP),
+    ("umklapp-shifts-only-up-to-1",
+     "  for (int m0 = -2; m0 <= 2; ++m0)\n    for (int m1 = -2; m1 <= 2; ++m1)\n      for (int m2 = -2; m2 <= 2; ++m2) {",
+     "  for (int m0 = -1; m0 <= 1; ++m0)\n    for (int m1 = -1; m1 <= 1; ++m1)\n      for (int m2 = -1; m2 <= 1; ++m2) {",
+     UMKLAPP),
+    # a partner of zero frequency kept (reading: such terms are skipped)
+    ("zero-frequency-partner-kept", "if (w3 == 0.0) continue;", "", [RATES]),
 ]
 
 # (name, file under oracle/, text, replacement, pins): each text occurs exactly once in its file

@@ -272,3 +272,43 @@ def test_umklapp_classification_is_point_group_invariant(rng):
             for R in ops[::5]:
                 assert oracle.umklapp(cr, idx(R @ G[q]), idx(R @ G[q1]), idx(R @ G[q2]), pr) == u
     assert seen == {0, 1}
+
+
+def test_umklapp_reading_on_a_sheared_cell(rng):
+    """On a strongly sheared cell the shortest translate of some grid wavevectors needs a shift of 2 reciprocal
+    vectors.  The classification must follow the reading exactly: a brute-force search written here (shortest
+    sum_a (g_a / N_a - m_a) b_a over m_a in [-2, 2], ties to the lexicographically smallest m) gives every
+    representative, and Q = 0 decides normal against Umklapp for every process of the grid."""
+    import itertools
+    a = 3.0
+    lattice = a * np.array([[1.0, -5.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    cr = synth.simple_cubic((4, 4, 2)).with_grid((4, 4, 2))
+    cr.lattice = lattice
+    grid = np.array(cr.grid)
+    B = 2.0 * np.pi * np.linalg.inv(lattice).T
+    shifts = sorted(itertools.product(range(-2, 3), repeat=3))      # lexicographic order
+    G = np.array(np.unravel_index(np.arange(cr.nq), cr.grid)).T
+    rep = np.zeros((cr.nq, 3))
+    need2 = 0
+    for q in range(cr.nq):
+        best, bm = None, None
+        for m in shifts:
+            k = (G[q] / grid - np.array(m)) @ B
+            l2 = float(k @ k)
+            if best is None or l2 < best * (1.0 - 1e-9):
+                best, bm = l2, m
+        rep[q] = G[q] / grid - np.array(bm)                          # reduced coordinates of the representative
+        need2 += max(abs(x) for x in bm) == 2
+    assert need2 > 0                                                 # the cell exercises shifts of 2
+    idx = lambda g: int(((g[0] % grid[0]) * grid[1] + g[1] % grid[1]) * grid[2] + g[2] % grid[2])
+    signs = {0: (1, 1), 1: (1, -1), 2: (-1, -1)}
+    seen = set()
+    for _ in range(400):
+        q, q1, q2 = (int(x) for x in rng.integers(0, cr.nq, size=3))
+        for pr, (s1, s2) in signs.items():
+            q3 = idx(G[q] + s1 * G[q1] + s2 * G[q2])
+            Q = rep[q] + s1 * rep[q1] + s2 * rep[q2] - rep[q3]
+            expect = int(np.abs(Q).max() > 1e-9)
+            assert oracle.umklapp(cr, q, q1, q2, pr) == expect, (q, q1, q2, pr)
+            seen.add(expect)
+    assert seen == {0, 1}
