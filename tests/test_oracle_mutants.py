@@ -124,6 +124,10 @@ PY_MUTANTS = [
     ("modes-partner-velocity-not-negated", "modes.py", "w, U.T.conj(), -v", "w, U.T.conj(), v", [MODES]),
     ("modes-eigenvectors-as-rows-not-columns", "modes.py", "om[q], ev[q], ve[q] = w, U.T, v",
      "om[q], ev[q], ve[q] = w, U, v", [MODES]),
+    ("modes-velocities-not-averaged-over-degenerate-sets", "modes.py",
+     "v[k] = 0.0 if w[k] == 0.0 else CONV * avg / (2.0 * w[k])",
+     "v[k] = 0.0 if w[k] == 0.0 else CONV * raw[k] / (2.0 * w[k])", [MODES, RATES]),
+    ("modes-gamma-acoustic-not-zeroed", "modes.py", "if q == 0 and b < 3:", "if False:", [MODES, RATES]),
     ("kappa-heat-capacity-without-x", "__init__.py", "c = x * x * np.exp(x) / np.expm1(x) ** 2",
      "c = x * np.exp(x) / np.expm1(x) ** 2", [KAPPA]),
     ("kappa-without-the-cell-volume", "__init__.py", "/ (N * V)", "/ N", [KAPPA]),
