@@ -97,7 +97,15 @@ C_MUTANTS = [
     ("v3-third-leg-not-conjugated", "ea * eb * conj(orc_e(p, q2, j2, c));", "ea * eb * orc_e(p, q2, j2, c);", [RATES3]),
     ("rates3-sigma-at-the-mode", "orc_sigma(&P, vel + 3 * (q1 * nb + j1), vel + 3 * (q2 * nb + j2), scalebroad, dq, dq_mode);",
      "orc_sigma(&P, vel + 3 * (q * nb + j), vel + 3 * (q2 * nb + j2), scalebroad, dq, dq_mode);", [RATES3]),
+    ("rates3-gaussian-without-sqrt-pi",
+     "(sqrt(M_PI) * sigma);\n              double v2 = 1.0;\n              if (!unit_vertex) {\n                if (!have_phi) {\n"
+     "                  orc_phi3",
+     "(sigma);\n              double v2 = 1.0;\n              if (!unit_vertex) {\n                if (!have_phi) {\n"
+     "                  orc_phi3", [RATES3]),
     # three-phonon-like phase space P3 / WP3
+    ("phase3-gaussian-normalised-by-sigma-squared",
+     "(sqrt(M_PI) * sigma);\n            acc_p += (sgn > 0 ? 1.0 : 0.5) * delta;",
+     "(sqrt(M_PI) * sigma * sigma);\n            acc_p += (sgn > 0 ? 1.0 : 0.5) * delta;", [PHASE3, RATES3]),
     ("phase3-minus-weight-1", "acc_p += (sgn > 0 ? 1.0 : 0.5) * delta;", "acc_p += delta;", [PHASE3]),
     ("phase3-wp3-plus-weight", "const double B = (sgn > 0) ? (n1 - n2) : 0.5 * (n1 + n2 + 1.0);",
      "const double B = (sgn > 0) ? (n1 + n2) : 0.5 * (n1 + n2 + 1.0);", [PHASE3]),

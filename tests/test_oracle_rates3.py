@@ -120,3 +120,59 @@ def test_single_q_closed_form_in_si_units(rng):
                     expect += (1.0 if pr == 0 else 0.5) * gam
         assert rates[0, lam] == pytest.approx(expect * 1e-12, rel=1e-9, abs=1e-300), lam
     assert np.array_equal(acc, count) and acc.min() > 0
+
+
+def swept_delta3(cr, s_values, sb, dq_mode, va, vb, which):
+    """delta(s) of the three-phonon paths, extracted on a crystal whose mode (q = 0, j = 0) has omega = 1, with
+    omega(q = 0) = (1, 1, 2 + s) and omega = (50, 60, 70) at every other grid point.
+
+    (+) terms of that mode: dw = (1 + w') - w''.  With q' = q'' = 0, j' in {0, 1} and j'' = 2 it is -s and sigma =
+    sb |v(0 or 1) - v(2)| |dq|; every other term misses energy conservation by 1 or more, outside the window for the
+    sigma used here.  which = "p3": P3 = (1/N) sum [delta+ + 1/2 delta-] holds 2 delta / N; which = "rates3": the
+    unit-vertex three-phonon sum (1/N) sum B+ delta / (w w' w'') with B+ = n' - n'' holds 2 (n(1) - n(2 + s))
+    delta / (N (2 + s)), with the oracle's Bose factor (pinned against the SI definition elsewhere)."""
+    N = cr.nq
+    evec = np.tile(np.eye(3, dtype=complex)[None], (N, 1, 1))
+    vel = np.zeros((N, 3, 3))
+    vel[0] = [va, va, vb]
+    T = 300.0
+    out = []
+    for s in s_values:
+        omega = np.tile(np.array([[50.0, 60.0, 70.0]]), (N, 1))
+        omega[0] = [1.0, 1.0, 2.0 + s]
+        if which == "p3":
+            p3, _ = oracle.phase3(cr, omega, vel, temps=[T], scalebroad=sb, window=2.0, dq_mode=dq_mode, sel=[0])
+            out.append(p3[0] * N / 2.0)
+        else:
+            r, acc = oracle.rates3(cr, omega, evec, vel, temps=[T], scalebroad=sb, window=2.0, dq_mode=dq_mode,
+                                   sel=[0], unit_vertex=True)
+            assert acc[0] in (0.0, 2.0) and acc[1] == 0.0
+            weight = 2.0 * (oracle.bose(1.0, T) - oracle.bose(2.0 + s, T)) / (2.0 + s)
+            out.append(r[0, 0] * N / weight)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("which", ["p3", "rates3"])
+@pytest.mark.parametrize("dq_mode", [0, 1])
+def test_three_phonon_gaussian_is_normalised_and_its_width_is_the_hand_sigma(which, dq_mode):
+    """The Gaussian of the three-phonon paths (Eq. 3phgamma with the broadening of Sec. 2.4 at the two partners),
+    fixed by mathematics as for the four-phonon rates: peak 1/(sqrt(pi) sigma), e^-1 at s = sigma, support ending at
+    window sigma, and a midpoint sum over s equal to erf(window), the mass of a normalised Gaussian; sigma worked
+    out by hand from the orthorhombic cell, the grid and the injected velocities."""
+    from test_oracle_delta import grid_crystal, hand_sigma
+    lattice, grid = np.diag([3.0, 4.0, 5.0]), (2, 3, 1)
+    va, vb, sb = (0.3, -0.2, 0.5), (0.0, 0.1, -0.1), 0.6
+    cr = grid_crystal(lattice, grid)
+    sig = hand_sigma(lattice, grid, [va[k] - vb[k] for k in range(3)], sb, dq_mode)
+    assert 0.05 < sig < 0.45   # the window edge stays inside the gap of 1 to the other terms
+    d = swept_delta3(cr, [0.0, sig, -1.5 * sig], sb, dq_mode, va, vb, which)
+    assert d[0] == pytest.approx(1.0 / (np.sqrt(np.pi) * sig), rel=1e-12)
+    assert d[1] / d[0] == pytest.approx(np.exp(-1.0), rel=1e-9)
+    assert d[2] / d[0] == pytest.approx(np.exp(-2.25), rel=1e-9)
+    edge = swept_delta3(cr, [2.0 * sig * (1 - 1e-7), 2.0 * sig * (1 + 1e-7)], sb, dq_mode, va, vb, which)
+    assert edge[0] > 0 and edge[1] == 0.0
+    n = 800
+    h = 4.4 * sig / n
+    s = -2.2 * sig + h * (np.arange(n) + 0.5)
+    mass = float(np.sum(swept_delta3(cr, s, sb, dq_mode, va, vb, which)) * h)
+    assert mass == pytest.approx(float(__import__("math").erf(2.0)), abs=2e-4)
