@@ -67,6 +67,8 @@ C_MUTANTS = [
     ("multiplicity-splitting-1/2", "{0.5, 0.5, 1.0 / 6.0}", "{0.5, 0.5, 0.5}", CLOSED),
     ("multiplicity-recombination-1", "{0.5, 0.5, 1.0 / 6.0}", "{1.0, 0.5, 1.0 / 6.0}", CLOSED),
     ("frequency-product-without-w'''", "v2 * delta / (w * w1 * w2 * w3)", "v2 * delta / (w * w1 * w2)", CLOSED),
+    ("unit-conversion-off-by-ten", "return ORC_ECHARGE / ORC_AMU * 1e20 * 1e-24;",
+     "return ORC_ECHARGE / ORC_AMU * 1e20 * 1e-23;", CLOSED),
     ("prefactor-hbar-not-squared", "const double pref = M_PI * ORC_HBAR * ORC_HBAR * conv",
      "const double pref = M_PI * ORC_HBAR * conv", CLOSED),
     ("energy-difference-sign-of-q'", "double t = (s1 > 0) ? (w + w1) : (w - w1);",
@@ -136,6 +138,8 @@ PY_MUTANTS = [
      "v[k] = 0.0 if w[k] == 0.0 else CONV * avg / (2.0 * w[k])",
      "v[k] = 0.0 if w[k] == 0.0 else CONV * raw[k] / (2.0 * w[k])", [MODES, RATES]),
     ("modes-gamma-acoustic-not-zeroed", "modes.py", "if q == 0 and b < 3:", "if False:", [MODES, RATES]),
+    ("modes-unit-conversion-off-by-ten", "modes.py", "CONV = ECHARGE / AMU * 1e20 * 1e-24",
+     "CONV = ECHARGE / AMU * 1e20 * 1e-23", [MODES]),
     ("kappa-heat-capacity-without-x", "__init__.py", "c = x * x * np.exp(x) / np.expm1(x) ** 2",
      "c = x * np.exp(x) / np.expm1(x) ** 2", [KAPPA]),
     ("kappa-without-the-cell-volume", "__init__.py", "/ (N * V)", "/ N", [KAPPA]),
