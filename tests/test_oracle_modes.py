@@ -119,3 +119,18 @@ def test_gamma_acoustic_zero_and_stable():
         assert np.all(w[0, :3] == 0.0)
         assert np.all(w[0, 3:] > 0.0)
         assert np.all(w[1:] > 0.0)
+
+
+@pytest.mark.parametrize("maker", [lambda: synth.zincblende_bas((2, 2, 2)), lambda: synth.diamond_si((2, 2, 2))])
+def test_gamma_optical_frequency_is_the_reduced_mass_closed_form(maker):
+    """Two atoms per cell, nearest-neighbour springs along the four tetrahedral bonds n (central k_c = 1, transverse
+    k_t = 0.25 eV/A^2) and next-nearest springs within each sublattice: at Gamma the sublattice springs cancel by
+    the sum rule, the bonds give the coupling block a I with a = k_c sum n n^T + k_t sum (I - n n^T) = 4/3 k_c +
+    8/3 k_t, and the three optical modes have omega^2 = a (1/M_1 + 1/M_2) (the textbook diatomic result with the
+    reduced mass); the acoustic ones are zero."""
+    cr = maker()
+    w, e, v = oracle_modes(cr)
+    a = 4.0 / 3.0 * 1.0 + 8.0 / 3.0 * 0.25
+    w_opt = np.sqrt(a * (1.0 / cr.mass[0] + 1.0 / cr.mass[1]) * TO_PS2)
+    assert np.all(w[0, :3] == 0.0)
+    np.testing.assert_allclose(w[0, 3:], w_opt, rtol=1e-12)
