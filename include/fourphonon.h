@@ -42,7 +42,7 @@ extern "C" {
 #define FP_PREC_MIXED 1 /* vertex and Gaussian in FP32, window decisions exact, sums in FP64 */
 #define FP_PREC_DOUBLE_FLOAT 2 /* FP64 path whose vertex contraction (Eq. V4 assembly and the two contractions)
                                   runs on the FP32 pipes in double-float: pairs of floats with exact high products
-                                  (fma residual) and two-sum accumulation, about 2^-48 per operation; window
+                                  (fma residual) and two-sum accumulation, about 2^-46 per operation; window
                                   decisions, Gaussian, Bose factors and sums as in FP_PREC_FP64 */
 
 typedef struct fp_ctx fp_ctx;

@@ -31,7 +31,7 @@
 // Precision of the instantiations:
 //   double: vertex, sigma, dw, Gaussian (table-driven exp), Bose weights and sums in FP64.
 //   double with DF = true: as double, but the vertex assembly and both contractions run in double-float
-//           (pairs of floats, about 2^-48 per operation) on the FP32 pipes, and with one temperature so do the
+//           (pairs of floats, about 2^-46 per operation) on the FP32 pipes, and with one temperature so do the
 //           accepted terms (dw from two-float frequencies, Gaussian, Bose and row weights, running sums that
 //           move into FP64 sums at fixed points); window decisions and sums across lanes and items stay FP64.
 //   float:  vertex assembly and contraction in FP32; dw from two-float frequencies (error-free sums,
@@ -115,7 +115,7 @@ __device__ __forceinline__ float ld_fc<float>(const RatesArgs& a, size_t i) {
 // Double-float arithmetic for the FP64-accurate vertex contraction of FP_PREC_DOUBLE_FLOAT: a real is a pair of
 // floats (h, l) with value h + l; a complex is a float4 (re.h, re.l, im.h, im.l).  A product keeps the high parts'
 // product exactly (fma residual) and the cross terms in FP32; a sum adds the high parts by Knuth's two-sum and the
-// low parts in FP32, so each operation keeps about 48 bits (Dekker 1971; the pair is renormalised when stored).
+// low parts in FP32, so each operation keeps about 46 bits (Dekker 1971; the pair is renormalised when stored).
 __device__ __forceinline__ float4 cdf_from(double re, double im) {
   const float rh = __double2float_rn(re), ih = __double2float_rn(im);
   return make_float4(rh, __double2float_rn(re - (double)rh), ih, __double2float_rn(im - (double)ih));
@@ -161,7 +161,7 @@ __device__ __forceinline__ double cdf_abs2(float4 w) {
 }
 
 // Double-float reals (float2: x high, y low) for the accepted-term evaluation of FP_PREC_DOUBLE_FLOAT with one
-// temperature: the frequency difference, the Gaussian and the products run on the FP32 pipes at about 2^-47
+// temperature: the frequency difference, the Gaussian and the products run on the FP32 pipes at about 2^-46
 // relative error per operation.
 __device__ __forceinline__ float2 df_make(double v) {
   const float h = __double2float_rn(v);
@@ -215,8 +215,8 @@ constexpr float kAbsV = 1.0f / 1099511627776.0f;  // 2^-40: two-float velocity d
 // exp(-u) for the FP64 Gaussian, table-driven (P. T. P. Tang, ACM TOMS 15 (1989) 144-157), taking v = 64 u:
 // u = k h + r with h = 1/64, k = rint(v) and |r| <= h/2, exp(-u) = exp(-k h) exp(-r); exp(-k h) comes from a table
 // of kExpTab entries (0 <= u <= 4), exp(-r) from its Taylor polynomial of degree 5, whose truncation error
-// (h/2)^6/6! < 4e-16 is below two ulp. The polynomial runs in t = k - v = -64 r (exact: |t| <= 1/2 and k lies
-// within a factor 2 of v), with the coefficients 1/n! scaled by 64^-n, exact powers of two. Larger u (only when
+// (h/2)^6/6! = 3.2e-16 is about three units of 2^-53. The polynomial runs in t = k - v = -64 r (exact: |t| <= 1/2
+// and k lies within a factor 2 of v), with the coefficients 1/n! scaled by 64^-n, exact powers of two. Larger u (only when
 // the window exceeds 2) takes exp().
 constexpr double kSqrtPi = 1.7724538509055160273;  // sqrt(pi)
 constexpr int kExpTab = 264;

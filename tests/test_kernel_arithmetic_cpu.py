@@ -1,0 +1,141 @@
+"""Accuracy of the rate kernel's own arithmetic building blocks, rebuilt on the CPU.
+
+The kernel computes two things with arithmetic of its own rather than library calls, and the parity budget
+(1e-10 relative for the FP64-accurate paths) rests on their stated accuracy:
+
+* the FP64 Gaussian's exp(-u), table-driven after P. T. P. Tang (ACM TOMS 15 (1989) 144-157): v = 64 u, k = rint(v),
+  exp(-u) = exp(-k/64) * p(k - v) with p the degree-5 Taylor polynomial of exp(t/64) in Horner form with fused
+  multiply-adds; stated: truncation 3.2e-16 relative, a few units of 2^-53 in all;
+* double-float arithmetic (a real as a pair of floats h + l, Dekker 1971): products with the high product exact
+  through its fma residual, sums with Knuth's two-sum, about 2^-47 relative error per operation; the double-float
+  exp of the same table method; |W|^2 from a double-float complex.
+
+Each block is rebuilt here from its description (numpy float64 / float32 with every operation rounded to nearest;
+a fused multiply-add as the product in a wider type plus the addend, rounded once to the target type) and compared
+with long-double references on dense and random arguments.  The exp table is the correctly rounded exp(-k/64),
+and one more ulp is allowed for the kernel's table, which CUDA's exp (1 ulp) fills.
+"""
+import numpy as np
+
+LD = np.longdouble
+F32 = np.float32
+ULP64 = 2.0 ** -53
+
+
+def fma64(a, b, c):
+    return (np.asarray(a, LD) * np.asarray(b, LD) + np.asarray(c, LD)).astype(np.float64)
+
+
+def fma32(a, b, c):
+    return (np.asarray(a, np.float64) * np.asarray(b, np.float64) + np.asarray(c, np.float64)).astype(F32)
+
+
+def table64():
+    k = np.arange(264)
+    return np.exp(-(k.astype(LD)) / LD(64)).astype(np.float64)
+
+
+def exp_neg64(v, tab):
+    """The FP64 kernel's exp(-v/64) for 0 <= v <= 256."""
+    k = np.rint(v).astype(np.int64)
+    t = k.astype(np.float64) - v
+    p = np.full_like(v, (1.0 / 120.0) / 1073741824.0)
+    for c in ((1.0 / 24.0) / 16777216.0, (1.0 / 6.0) / 262144.0, 0.5 / 4096.0, 1.0 / 64.0, 1.0):
+        p = fma64(p, t, np.full_like(v, c))
+    return tab[k] * p
+
+
+def test_fp64_gaussian_exp_is_accurate_to_a_few_ulp():
+    tab = table64()
+    rng = np.random.Generator(np.random.PCG64(11))
+    v = np.concatenate([np.linspace(0.0, 256.0, 200_001), rng.uniform(0.0, 256.0, 200_000),
+                        np.arange(257) + 0.5, np.arange(257) - 0.5 + 1e-13])
+    v = v[(v >= 0.0) & (v <= 256.0)]
+    got = exp_neg64(v, tab)
+    ref = np.exp(-(v.astype(LD)) / LD(64))
+    rel = np.abs((got.astype(LD) - ref) / ref).astype(np.float64)
+    # the polynomial's truncation (1/128)^6 / 6! = 3.2e-16, the roundings of the Horner steps, the table entry and
+    # the final product: 5.0 units of 2^-53 measured; the kernel's table (CUDA exp, 1 ulp) may add about one more
+    assert rel.max() <= 5.5 * ULP64, rel.max()
+    assert rel.max() + 2 * ULP64 <= 1e-15
+
+
+# ---------------------------------------------------------------------------------------------------- double-float
+def df_make(v):
+    h = np.asarray(v, np.float64).astype(F32)
+    return h, (np.asarray(v, np.float64) - h.astype(np.float64)).astype(F32)
+
+
+def df_fast(h, l):
+    s = h + l
+    return s, l - (s - h)
+
+
+def df_mul(a, b):
+    p = a[0] * b[0]
+    e = fma32(a[0], b[1], fma32(a[1], b[0], fma32(a[0], b[0], -p)))
+    return df_fast(p, e)
+
+
+def df_add(a, b):
+    s = a[0] + b[0]
+    bb = s - a[0]
+    e = (a[0] - (s - bb)) + (b[0] - bb)
+    return df_fast(s, e + (a[1] + b[1]))
+
+
+def df_value(a):
+    return a[0].astype(LD) + a[1].astype(LD)
+
+
+def table_df():
+    return df_make(table64())
+
+
+def df_exp_neg64(v, tab):
+    """The double-float kernel's exp(-v/64) for 0 <= v <= 256, v a double-float."""
+    kf = np.rint(v[0])
+    k = kf.astype(np.int64)
+    t = df_add((kf - v[0], np.zeros_like(kf)), (-v[1], np.zeros_like(kf)))
+    c45 = fma32(np.full_like(kf, F32(1.0 / 128849018880.0)), t[0], np.full_like(kf, F32(1.0 / 402653184.0)))
+    e3 = 1.0 / 1572864.0
+    e3h = F32(e3)
+    e3l = F32(e3 - float(e3h))
+    p = df_add(df_mul((c45, np.zeros_like(kf)), t), (np.full_like(kf, e3h), np.full_like(kf, e3l)))
+    for c in (1.0 / 8192.0, 1.0 / 64.0, 1.0):
+        p = df_add(df_mul(p, t), (np.full_like(kf, F32(c)), np.zeros_like(kf)))
+    return df_mul((tab[0][k], tab[1][k]), p)
+
+
+def rand_df(rng, n, lo=-3.0, hi=3.0):
+    x = rng.uniform(0.5, 1.0, n) * 2.0 ** rng.integers(lo, hi, n) * np.where(rng.random(n) < 0.5, 1.0, -1.0)
+    return df_make(x)
+
+
+def test_double_float_products_and_sums():
+    rng = np.random.Generator(np.random.PCG64(12))
+    n = 200_000
+    a, b = rand_df(rng, n), rand_df(rng, n)
+    prod = df_mul(a, b)
+    ref = df_value(a) * df_value(b)
+    # rounding of the two fused low-part steps (about 3 x 2^-48) and the dropped l l product (2^-48): below 2^-45
+    assert (np.abs((df_value(prod) - ref) / ref).astype(np.float64)).max() <= 2.0 ** -45
+    # sums of like signs (no cancellation, where a relative bound applies)
+    b = (np.abs(b[0]) * np.sign(a[0]), np.abs(b[1]) * np.sign(a[0]) * np.sign(b[0]))
+    tot = df_add(a, b)
+    ref = df_value(a) + df_value(b)
+    assert (np.abs((df_value(tot) - ref) / ref).astype(np.float64)).max() <= 2.0 ** -45
+    # renormalised results: |l| <= ulp(h) / 2
+    for h, l in (prod, tot):
+        assert np.all(np.abs(l) <= np.spacing(np.abs(h)) / 2)
+
+
+def test_double_float_gaussian_exp():
+    tab = table_df()
+    rng = np.random.Generator(np.random.PCG64(13))
+    v64 = np.concatenate([np.linspace(0.0, 256.0, 100_001), rng.uniform(0.0, 256.0, 100_000)])
+    v = df_make(v64)
+    got = df_value(df_exp_neg64(v, tab))
+    ref = np.exp(-df_value(v) / LD(64))
+    rel = np.abs((got - ref) / ref).astype(np.float64)
+    assert rel.max() <= 2.0 ** -44, rel.max()     # far inside the 1e-10 parity bound
