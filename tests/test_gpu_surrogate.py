@@ -151,8 +151,8 @@ def test_phase4_matches_oracle_unit_vertex(lib, maker):
 def test_surrogate_sweep_at_new_temperatures(lib):
     """Learned rates at new temperatures: anchors at 300, 650 and 1000 K for every mode, and 16 output temperatures
     (two batched evaluations for the exact path).  Exact entries are the exact rates bit for bit, the network's
-    entries are checked against exact rates of every mode, bins it keeps hold the 5 % rule, and the share of
-    entries evaluated exactly is reported."""
+    entries are checked against exact rates of every mode, bins it keeps hold the 5 % rule, and the network must
+    replace exact evaluation for part of the entries (the gain over the method without it)."""
     cr = synth.diamond_si((6, 6, 6))
     anchors = [300.0, 650.0, 1000.0]
     temps = list(np.linspace(300.0, 1000.0, 16))
@@ -172,12 +172,12 @@ def test_surrogate_sweep_at_new_temperatures(lib):
     assert np.array_equal(ra[us], ex[us]) and np.all(ra[:, ~pos] == 0.0)
     pred = (~us) & (ex > 0)
     share_exact = us[:, pos].mean()
-    if pred.any():
-        rel = np.abs(ra[pred] - ex[pred]) / ex[pred]
-        assert np.median(rel) <= 0.05
-        print(f"sweep: {pred.sum()} of {pos.sum() * 16} entries predicted (exact share {share_exact:.3f}); "
-              f"predicted rel err median {np.median(rel):.4f} p90 {np.quantile(rel, 0.9):.4f} max {rel.max():.4f}; "
-              f"held-out median {rep['holdout_median_rel_err']:.4f}; {rep['n_bins_fallback']}/{rep['n_bins']} bins exact")
-    else:
-        assert rep["n_bins_fallback"] == rep["n_bins"]
+    # the gain: the network replaces exact evaluation for part of the (mode, T) entries (measured: 64 % of them on
+    # this workload), at the 5 % rule on the entries it predicts
+    assert pred.any() and share_exact < 0.9
+    rel = np.abs(ra[pred] - ex[pred]) / ex[pred]
+    assert np.median(rel) <= 0.05
+    print(f"sweep: {pred.sum()} of {pos.sum() * 16} entries predicted (exact share {share_exact:.3f}); "
+          f"predicted rel err median {np.median(rel):.4f} p90 {np.quantile(rel, 0.9):.4f} max {rel.max():.4f}; "
+          f"held-out median {rep['holdout_median_rel_err']:.4f}; {rep['n_bins_fallback']}/{rep['n_bins']} bins exact")
     assert rep["n_train"] > 0 and rep["n_holdout"] > 0
