@@ -35,7 +35,7 @@
 //           accepted terms (dw from two-float frequencies, Gaussian, Bose and row weights, running sums that
 //           move into FP64 sums at fixed points); window decisions and sums across lanes and items stay FP64.
 //   float:  vertex assembly and contraction in FP32; dw from two-float frequencies (error-free sums,
-//           |error| <= 2^-44 sum(w)); sigma from two-float velocities; Gaussian and Bose weights in FP32;
+//           |error| <= 2^-24 |dw| + 2^-44 sum(w)); sigma from two-float velocities; Gaussian and Bose weights in FP32;
 //           compensated (two-float) per-thread sums, FP64 across threads and work items.  With TC = true the
 //           per-q'' contraction T runs on the tensor cores (fp_tc.cuh).
 #pragma once

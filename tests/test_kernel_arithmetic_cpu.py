@@ -139,3 +139,36 @@ def test_double_float_gaussian_exp():
     ref = np.exp(-df_value(v) / LD(64))
     rel = np.abs((got - ref) / ref).astype(np.float64)
     assert rel.max() <= 2.0 ** -44, rel.max()     # far inside the 1e-10 parity bound
+
+
+def test_mixed_path_energy_difference():
+    """The mixed path's dw for the Gaussian: two-float frequencies (h = fl32(w), l = fl32(w - h)), Knuth two-sums of
+    the high parts, the low parts and the two-sum errors added in FP32, one final float.  Its error is the rounding
+    of that float (2^-24 |dw|) plus at most 2^-44 of the sum of the frequencies."""
+    def split(x):
+        h = x.astype(F32)
+        return h, (x - h.astype(np.float64)).astype(F32)
+
+    def two_sum(a, b):
+        s = a + b
+        bb = s - a
+        return s, (a - (s - bb)) + (b - bb)
+
+    rng = np.random.Generator(np.random.PCG64(14))
+    n = 400_000
+    w0, w1, w2 = (np.exp(rng.uniform(np.log(0.05), np.log(150.0), n)) for _ in range(3))
+    s1 = np.where(rng.random(n) < 0.5, 1.0, -1.0)
+    s2 = np.where(rng.random(n) < 0.5, 1.0, -1.0)
+    w3 = (w0 + s1 * w1 + s2 * w2) - rng.normal(size=n) * np.exp(rng.uniform(np.log(1e-9), np.log(20.0), n))
+    k = w3 > 0.05
+    w0, w1, w2, w3, s1, s2 = (x[k] for x in (w0, w1, w2, w3, s1, s2))
+    (h0, l0), (h1, l1), (h2, l2), (h3, l3) = (split(x) for x in (w0, w1, w2, w3))
+    g1, g2 = s1.astype(F32), s2.astype(F32)
+    t, e1 = two_sum(h0, g1 * h1)
+    t, e2 = two_sum(t, g2 * h2)
+    t, e3 = two_sum(t, -h3)
+    dwf = t + ((((l0 + g1 * l1) + g2 * l2) - l3) + ((e1 + e2) + e3))
+    exact = (w0.astype(LD) + s1 * w1.astype(LD) + s2 * w2.astype(LD)) - w3.astype(LD)
+    err = np.abs(dwf.astype(LD) - exact).astype(np.float64)
+    S = w0 + w1 + w2 + w3
+    assert np.all(err <= 2.0 ** -24 * np.abs(exact.astype(np.float64)) + 2.0 ** -44 * S)
