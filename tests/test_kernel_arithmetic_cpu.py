@@ -144,7 +144,8 @@ def test_double_float_gaussian_exp():
 def test_mixed_path_energy_difference():
     """The mixed path's dw for the Gaussian: two-float frequencies (h = fl32(w), l = fl32(w - h)), Knuth two-sums of
     the high parts, the low parts and the two-sum errors added in FP32, one final float.  Its error is the rounding
-    of that float (2^-24 |dw|) plus at most 2^-44 of the sum of the frequencies."""
+    of that float (2^-24 |dw|) plus at most 2^-44 of the sum of the frequencies.  The double-float path keeps the
+    pair (high sum, low sum) instead of one float, which leaves at most 2^-46 of the sum."""
     def split(x):
         h = x.astype(F32)
         return h, (x - h.astype(np.float64)).astype(F32)
@@ -172,3 +173,6 @@ def test_mixed_path_energy_difference():
     err = np.abs(dwf.astype(LD) - exact).astype(np.float64)
     S = w0 + w1 + w2 + w3
     assert np.all(err <= 2.0 ** -24 * np.abs(exact.astype(np.float64)) + 2.0 ** -44 * S)
+    # the double-float path keeps dw as the exact pair (t, lo) of that two-sum: only the low parts' error is left
+    pair = t.astype(LD) + ((((l0 + g1 * l1) + g2 * l2) - l3) + ((e1 + e2) + e3)).astype(LD)
+    assert np.all(np.abs(pair - exact).astype(np.float64) <= 2.0 ** -46 * S)
